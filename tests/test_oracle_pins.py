@@ -1,0 +1,549 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+(product-form equilibrium, Gaussian moments, BGK equivalence), invariants the
+paper states (mass/momentum collision invariants, equilibrium fixed point),
+the paper's own second and third statements of the same objects (the boxed
+attractor list and the explicit Appendix D steps, stored under tests/golden/),
+and the Chapman-Enskog transport coefficients recovered from decaying waves.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CS2 = 1.0 / 3.0
+MNP = None
+
+
+def mnp():
+    global MNP
+    if MNP is None:
+        MNP = [tuple(int(v) for v in r) for r in O.moment_exponents()]
+    return MNP
+
+
+def idx(s):
+    return mnp().index(tuple(int(c) for c in s))
+
+
+def rand_f(seed, spread=0.5):
+    return W.random_populations(1, seed, spread)[:, 0]
+
+
+def central(f, u):
+    """Central moments measured by brute force (the instrument, not the oracle)."""
+    e = O.velocity_set().astype(float)
+    return np.array([np.sum(f * np.prod((e - u) ** np.array(k), axis=1)) for k in mnp()])
+
+
+def fields_of(f, F=(0, 0, 0)):
+    e = O.velocity_set().astype(float)
+    rho = f.sum()
+    u = (f @ e + 0.5 * np.asarray(F)) / rho
+    return rho, u
+
+
+# ---------------------------------------------------------------------------
+# Lattice and rest state
+# ---------------------------------------------------------------------------
+
+def test_velocity_set_is_d3q27_with_opposites():
+    e = O.velocity_set()
+    assert e.shape == (27, 3)
+    assert len({tuple(v) for v in e}) == 27
+    assert all(abs(c) <= 1 for c in e.ravel())
+    assert tuple(e[0]) == (0, 0, 0)
+    for v in e:
+        assert tuple(-v) in {tuple(w) for w in e}
+
+
+def test_rest_weights_exact():
+    """Reading G18: f^eq(1, 0) is the tensor product of (1/6, 2/3, 1/6)."""
+    f = O.equilibrium(1.0, [0.0, 0.0, 0.0])
+    e = O.velocity_set()
+    w1 = {-1: 1 / 6, 0: 2 / 3, 1: 1 / 6}
+    expect = np.array([w1[a] * w1[b] * w1[c] for a, b, c in e])
+    assert np.max(np.abs(f - expect)) < 1e-15
+    assert sorted(set(np.round(expect * 216).astype(int))) == [1, 4, 16, 64]
+    assert abs(f.sum() - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_is_product_form(seed):
+    """f^eq_a = rho prod_axes phi(e, u): phi(0) = 1 - cs2 - u^2, phi(+-1) = (cs2 + u^2 +- u)/2.
+    This is the per-axis solution of matching the Maxwellian central moments (1, 0, cs2)."""
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.8, 1.2)
+    u = rng.uniform(-0.2, 0.2, 3)
+    f = O.equilibrium(rho, u)
+    e = O.velocity_set()
+
+    def phi(c, v):
+        return 1 - CS2 - v * v if c == 0 else 0.5 * (CS2 + v * v + c * v)
+
+    expect = np.array([rho * phi(a, u[0]) * phi(b, u[1]) * phi(c, u[2]) for a, b, c in e])
+    assert np.max(np.abs(f - expect)) < 1e-15
+
+
+def test_maxwell_moments_are_gaussian_moments():
+    """Central moments of a Gaussian of variance cs2: rho cs2^k for (2,0,0)-type, (2,2,0), (2,2,2);
+    zero for any odd exponent (reading R3 reproduces the Maxwellian, Sec. 1 remark)."""
+    rho = 1.37
+    M = O.maxwell_moments(rho)
+    for m in range(3):
+        for n in range(3):
+            for p in range(3):
+                if m % 2 or n % 2 or p % 2:
+                    expect = 0.0
+                else:
+                    expect = rho * CS2 ** ((m + n + p) // 2)
+                assert abs(M[m, n, p] - expect) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Moment matrices against the explicit Appendix D steps (tests/golden)
+# ---------------------------------------------------------------------------
+
+def _read(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+def test_step1_projection_matches_paper():
+    """Appendix D Step 1 (printed) equals C(0) = P row by row."""
+    P = O.central_matrix([0, 0, 0])
+    rows = _read("appendixD_step1_raw_moments.txt")
+    assert len(rows) == 27
+    for r in rows:
+        row = np.zeros(27)
+        for t in r[1:]:
+            s, a = t.split("*f")
+            row[int(a)] += float(s)
+        assert np.array_equal(row, P[idx(r[0])]), r[0]
+
+
+def _poly_rows(name):
+    out = {}
+    for r in _read(name):
+        terms = []
+        for t in r[1:]:
+            c, pw, src, kind = t.split(":")
+            terms.append((int(c), tuple(int(ch) for ch in pw), src, kind))
+        out[r[0]] = terms
+    return out
+
+
+def _eval_row(terms, u, sources):
+    s = 0.0
+    for c, (a, b, d), src, kind in terms:
+        s += c * u[0] ** a * u[1] ** b * u[2] ** d * sources[kind][idx(src)]
+    return s
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_step2_frame_transform_matches_paper(seed):
+    """Appendix D Step 2 (printed binomial chain) reproduces the oracle's kappa = C(u) f,
+    except row 211, whose printed u_x^2 kappa_011 term is a raw moment (reading G2)."""
+    rng = np.random.default_rng(seed)
+    f = rand_f(seed)
+    u = rng.uniform(-0.3, 0.3, 3)
+    raw = O.central_matrix([0, 0, 0]) @ f
+    cen = O.central_matrix(u) @ f
+    rows = _poly_rows("appendixD_step2_central_from_raw.txt")
+    assert len(rows) == 27
+    for tgt, terms in rows.items():
+        literal = _eval_row(terms, u, {"Kps": raw, "Ks": cen})
+        if tgt == "211":
+            assert abs(literal - cen[idx(tgt)]) > 1e-6  # the printed row is a typo
+            fixed = _eval_row(terms, u, {"Kps": raw, "Ks": raw})
+            assert abs(fixed - cen[idx(tgt)]) < 1e-14
+        else:
+            assert abs(literal - cen[idx(tgt)]) < 1e-14, tgt
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_step4_inverse_transform_matches_paper(seed):
+    """Appendix D Step 4 (printed) reproduces P C(u)^-1 applied to central moments, except
+    row 211 (pre-collision kappa_011 printed, reading G3) and the sign of the
+    u_x u_y^2 kappa~_001 term of row 121 (reading G4)."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-0.3, 0.3, 3)
+    kt = rng.normal(size=27)
+    kpre = rng.normal(size=27)
+    raw_expect = O.central_matrix([0, 0, 0]) @ np.linalg.solve(O.central_matrix(u), kt)
+    rows = _poly_rows("appendixD_step4_raw_from_central.txt")
+    assert len(rows) == 27
+    for tgt, terms in rows.items():
+        literal = _eval_row(terms, u, {"Kts": kt, "Ks": kpre})
+        if tgt == "211":
+            assert abs(literal - raw_expect[idx(tgt)]) > 1e-6
+            fixed = _eval_row(terms, u, {"Kts": kt, "Ks": kt})
+            assert abs(fixed - raw_expect[idx(tgt)]) < 1e-13
+        elif tgt == "121":
+            assert abs(literal - raw_expect[idx(tgt)]) > 1e-6
+            fixed_terms = [(-c if (p == (1, 2, 0) and s == "001") else c, p, s, k) for c, p, s, k in terms]
+            assert abs(_eval_row(fixed_terms, u, {"Kts": kt}) - raw_expect[idx(tgt)]) < 1e-13
+        else:
+            assert abs(literal - raw_expect[idx(tgt)]) < 1e-13, tgt
+
+
+def test_step5_inverse_projection_matches_paper():
+    """Appendix D Step 5 (printed P^-1) equals the numerical inverse of C(0), except the sign of
+    kappa~'_010 in f~_4 (e_4 = -y; reading G7)."""
+    Pinv = np.linalg.inv(O.central_matrix([0, 0, 0]))
+    rows = _read("appendixD_step5_populations.txt")
+    assert len(rows) == 27
+    for r in rows:
+        a, den = int(r[0]), float(r[1])
+        row = np.zeros(27)
+        for t in r[2:]:
+            c, src = t.split(":")
+            row[idx(src)] += float(c) / den
+        if a == 4:
+            assert not np.allclose(row, Pinv[a])
+            row[idx("010")] = -row[idx("010")]
+        assert np.max(np.abs(row - Pinv[a])) < 1e-14, a
+
+
+def test_step3_group_decomposition_matches_paper():
+    """The inverse of the grouping matrix equals the decompositions printed in Step 3
+    (with kappa~_021 for the printed kappa~_112 of the third-order list, reading G5)."""
+    G = O.grouping_matrix()
+    Ginv = np.linalg.inv(G)
+    # group indices, Step 3 numbering
+    g = {n: j for j, n in enumerate(
+        "000 100 010 001 110 101 011 2s1 2d1 2d2 3s1 3m1 3s2 3m2 3s3 3m3 111 4s1 4d1 4d2 "
+        "211 121 112 122 212 221 222".split())}
+    printed = {
+        "200": {"2s1": 1 / 3, "2d1": 1 / 3, "2d2": 1 / 3},
+        "020": {"2s1": 1 / 3, "2d1": -2 / 3, "2d2": 1 / 3},
+        "002": {"2s1": 1 / 3, "2d1": 1 / 3, "2d2": -2 / 3},
+        "120": {"3s1": 0.5, "3m1": 0.5}, "102": {"3s1": 0.5, "3m1": -0.5},
+        "210": {"3s2": 0.5, "3m2": 0.5}, "012": {"3s2": 0.5, "3m2": -0.5},
+        "201": {"3s3": 0.5, "3m3": 0.5}, "021": {"3s3": 0.5, "3m3": -0.5},
+        "220": {"4s1": 0.25, "4d1": 0.25, "4d2": 0.5},
+        "202": {"4s1": 0.25, "4d1": 0.25, "4d2": -0.5},
+        "022": {"4s1": 0.5, "4d1": -0.5},
+    }
+    for tgt, coeffs in printed.items():
+        row = np.zeros(27)
+        for name, c in coeffs.items():
+            row[g[name]] = c
+        assert np.max(np.abs(Ginv[idx(tgt)] - row)) < 1e-15, tgt
+    for name in "000 100 010 001 110 101 011 111 211 121 112 122 212 221 222".split():
+        assert G[g[name], idx(name)] == 1.0 and abs(G[g[name]]).sum() == 1.0
+
+
+# ---------------------------------------------------------------------------
+# Attractors: generic formula against the boxed list
+# ---------------------------------------------------------------------------
+
+def _boxed(Pt, rho, fix_g1=True):
+    """The boxed discrete attractors of Sec. 3 / Step 3 of Appendix D, typed from the paper."""
+    k = lambda s: Pt[int(s[0]), int(s[1]), int(s[2])]  # noqa: E731
+    out = {
+        "220": (k("200") * k("020") + 2 * k("110") ** 2) / rho,
+        "202": (k("200") * k("002") + 2 * k("101") ** 2) / rho,
+        "022": (k("020") * k("002") + 2 * k("011") ** 2) / rho,
+        "211": (k("200") * k("011") + 2 * k("110") * k("101")) / rho,
+        "121": (k("020") * k("101") + 2 * k("110") * k("011")) / rho,
+        "112": (k("002") * k("110") + 2 * k("011") * k("101")) / rho,
+        "122": 2 / (5 * rho) * (k("020") * k("102") + k("002") * k("120") + 4 * k("011") * k("111")
+                                + 2 * (k("101") * k("021") + (k("110") if fix_g1 else k("011")) * k("012"))),
+        "212": 2 / (5 * rho) * (k("200") * k("012") + k("002") * k("210") + 4 * k("101") * k("111")
+                                + 2 * (k("110") * k("102") + k("011") * k("201"))),
+        "221": 2 / (5 * rho) * (k("200") * k("021") + k("020") * k("201") + 4 * k("110") * k("111")
+                                + 2 * (k("011") * k("210") + k("101") * k("120"))),
+        "222": 1 / (3 * rho) * (k("200") * k("022") + k("020") * k("202") + k("002") * k("220")
+                                + 4 * (k("110") * k("112") + k("101") * k("121") + k("011") * k("211"))),
+    }
+    return out
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_generic_attractor_matches_boxed_list(seed):
+    """Eq. (Mvcmattractor3D) with D' = kappa~_ij / rho reproduces the boxed attractors of orders
+    4-6; the printed kappa~_011 kappa~_012 term of kappa^Mv_122 is the continuous
+    Pi_110 Pi_012 (reading G1)."""
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.8, 1.2)
+    Pt = rng.normal(size=(3, 3, 3))
+    Pt[0, 0, 0] = rho
+    D = np.array([[Pt[2, 0, 0], Pt[1, 1, 0], Pt[1, 0, 1]],
+                  [Pt[1, 1, 0], Pt[0, 2, 0], Pt[0, 1, 1]],
+                  [Pt[1, 0, 1], Pt[0, 1, 1], Pt[0, 0, 2]]]) / rho
+    boxed = _boxed(Pt, rho)
+    for s, v in boxed.items():
+        m, n, p = (int(c) for c in s)
+        assert abs(O.attractor_generic(m, n, p, Pt, D) - v) < 1e-14 * max(1, abs(v)), s
+    literal = _boxed(Pt, rho, fix_g1=False)["122"]
+    assert abs(O.attractor_generic(1, 2, 2, Pt, D) - literal) > 1e-6
+
+
+def test_low_order_attractors_with_isotropic_diffusion():
+    """Orders <= 3: attractors rho; 0; cs2 rho on the diagonal, 0 off it; 0 at third order."""
+    rho = 1.1
+    Pi = np.zeros((3, 3, 3))
+    Pi[0, 0, 0] = rho
+    D = CS2 * np.eye(3)
+    assert abs(O.attractor_generic(0, 0, 0, Pi, D) - rho) < 1e-16
+    for s in ("100", "010", "001", "110", "101", "011", "120", "111", "021"):
+        assert O.attractor_generic(*(int(c) for c in s), Pi, D) == 0.0
+    for s in ("200", "020", "002"):
+        assert abs(O.attractor_generic(*(int(c) for c in s), Pi, D) - CS2 * rho) < 1e-16
+
+
+# ---------------------------------------------------------------------------
+# Collision: invariants and special cases with closed forms
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_collision_invariants(seed):
+    """Mass is conserved and momentum changes by exactly F (Step 7 half-force + sigma_100 = F_x),
+    for any omega_0..omega_26 in (0, 2) and either diffusion mode."""
+    rng = np.random.default_rng(100 + seed)
+    f = rand_f(seed)
+    F = rng.uniform(-1e-2, 1e-2, 3)
+    om = rng.uniform(0.05, 1.95, 27)
+    e = O.velocity_set().astype(float)
+    for mode in (O.EQ_MODE_FP, O.EQ_MODE_MCM):
+        ft = O.collide(f, F, om, mode)
+        assert abs(ft.sum() - f.sum()) < 1e-15
+        assert np.max(np.abs(ft @ e - (f @ e + F))) < 1e-15
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_equilibrium_is_a_fixed_point(mode):
+    """Collision leaves f^eq(rho, u) unchanged for any rates (F = 0)."""
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        feq = O.equilibrium(rng.uniform(0.9, 1.1), rng.uniform(-0.1, 0.1, 3))
+        ft = O.collide(feq, (0, 0, 0), rng.uniform(0.1, 1.9, 27), mode)
+        assert np.max(np.abs(ft - feq)) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mcm_with_equal_rates_is_bgk(seed):
+    """Relaxing every central moment at one rate toward Maxwellian central moments is linear:
+    f~ = f + w (f^eq - f) (BGK with the product-form equilibrium)."""
+    rng = np.random.default_rng(seed)
+    f = rand_f(seed)
+    w = rng.uniform(0.2, 1.9)
+    rho, u = fields_of(f)
+    ft = O.collide(f, (0, 0, 0), np.full(27, w), O.EQ_MODE_MCM)
+    expect = f + w * (O.equilibrium(rho, u) - f)
+    assert np.max(np.abs(ft - expect)) < 2e-15
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fp_with_unit_rates_lands_on_equilibrium(seed):
+    """With every omega = 1 the chain resets order 2 to its attractor, so the order 4 and 6
+    attractors become cs^4 rho and cs^6 rho: f~ = f^eq(rho, u)."""
+    f = rand_f(seed)
+    rho, u = fields_of(f)
+    ft = O.collide(f, (0, 0, 0), np.ones(27), O.EQ_MODE_FP)
+    assert np.max(np.abs(ft - O.equilibrium(rho, u))) < 2e-15
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fp_chain_uses_post_collision_moments(seed):
+    """Reading R2: with orders 4, 5, 6 fully relaxed (rates 1) and orders 2, 3 only partly, every
+    moment of order 4-6 of f~ equals the boxed attractor evaluated on the post-collision lower
+    moments of f~ itself (measured by brute force), not on the incoming ones."""
+    rng = np.random.default_rng(50 + seed)
+    f = rand_f(seed, spread=0.9)
+    rho, u = fields_of(f)
+    om = np.ones(27)
+    om[4:10] = rng.uniform(0.3, 1.7, 6)    # second order
+    om[10:17] = rng.uniform(0.3, 1.7, 7)   # third order
+    ft = O.collide(f, (0, 0, 0), om, O.EQ_MODE_FP)
+    k = central(ft, u)
+    Pt = np.zeros((3, 3, 3))
+    for i, (m, n, p) in enumerate(mnp()):
+        Pt[m, n, p] = k[i]
+    boxed = _boxed(Pt, rho)
+    for s_, v in boxed.items():
+        assert abs(k[idx(s_)] - v) < 1e-15, s_
+    # the incoming state is far from that
+    k0 = central(f, u)
+    assert abs(k0[idx("220")] - boxed["220"]) > 1e-4
+
+
+def test_third_order_attractors_vanish_under_force():
+    """Reading R1: with a body force the post-collision first moments are F/2, yet the third-order
+    attractors stay 0 (Step 3 list): with the third-order rates at 1, kappa~_3 = sigma_3 / 2,
+    where sigma is measured from the same collision with every rate 0."""
+    f = rand_f(8, spread=0.8)
+    F = np.array([4e-3, -3e-3, 2e-3])
+    rho, u = fields_of(f, F)
+    sig = O.central_matrix(u) @ (O.collide(f, F, np.zeros(27), O.EQ_MODE_FP) - f)
+    om = np.full(27, 0.8)
+    om[10:17] = 1.0
+    ft = O.collide(f, F, om, O.EQ_MODE_FP)
+    k = O.central_matrix(u) @ ft
+    for s_ in ("120", "102", "210", "012", "201", "021", "111"):
+        assert abs(k[idx(s_)] - 0.5 * sig[idx(s_)]) < 1e-14, s_
+        assert abs(sig[idx(s_)]) > 1e-6
+    assert abs(k[idx("100")] - 0.5 * F[0]) < 1e-14
+
+
+def test_source_moments_with_zero_rates_match_2d_list():
+    """With every omega = 0 the collision adds the source: C(u)(f~ - f) = sigma.  Its p = 0 moments
+    follow the printed 2D list (Eq. sourceCM2D): sigma_2 = 0, sigma_21 = 2 Fx/rho k_11 +
+    Fy/rho k_20, sigma_22 = 2(Fx/rho k_12 + Fy/rho k_21), and sigma_12 its mirror image."""
+    f = rand_f(5, spread=0.8)
+    F = np.array([3e-3, -2e-3, 0.0])
+    rho, u = fields_of(f, F)
+    ft = O.collide(f, F, np.zeros(27), O.EQ_MODE_FP)
+    sig = O.central_matrix(u) @ (ft - f)
+    k = central(f, u)
+    K = lambda s: k[idx(s)]  # noqa: E731
+    fx, fy = F[0] / rho, F[1] / rho
+    tol = 1e-14  # rounding of C(u)(f~ - f) with |f| ~ 1/27
+    assert abs(sig[idx("100")] - F[0]) < tol and abs(sig[idx("010")] - F[1]) < tol
+    for s in ("200", "020", "110"):
+        assert abs(sig[idx(s)]) < tol
+    assert abs(sig[idx("210")] - (2 * fx * K("110") + fy * K("200"))) < tol
+    # sigma_12 is the x<->y mirror of the printed sigma_21; the printed sigma_12 drops the
+    # factor n = 2 of Eq. (forcing:2D) on its F_y term (reading G19)
+    assert abs(sig[idx("120")] - (fx * K("020") + 2 * fy * K("110"))) < tol
+    assert abs(sig[idx("120")] - (fx * K("020") + fy * K("110"))) > 1e-6
+    assert abs(sig[idx("220")] - 2 * (fx * K("120") + fy * K("210"))) < tol
+    assert abs(sig[idx("210")]) > 1e-5  # non-trivial
+
+
+def test_rates_mapping():
+    om = O.rates(0.8, 0.0)
+    assert np.allclose(om[[4, 5, 6, 8, 9]], 1 / 0.8) and om[7] == 1.0
+    assert np.all(om[10:] == 1.0)
+    om = O.rates(0.8, 0.3)
+    assert np.allclose(om[10:17], 0.9) and np.allclose(om[17:23], 1.2)
+    assert np.allclose(om[23:26], 1.5) and np.isclose(om[26], 1.8)
+
+
+# ---------------------------------------------------------------------------
+# Lattice-level pins: conservation, transport coefficients (Appendix C)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_mass_conservation_over_steps(bc):
+    rho, ux, uy, uz = W.random_fields(6, 5, 4, seed=3, u_amp=0.03)
+    f = O.init_equilibrium(rho, ux, uy, uz)
+    g = O.run(f, 20, bc=bc, F=(1e-4, 0, 0), omega=O.rates(0.7))
+    assert abs(g.sum() - f.sum()) / f.sum() < 1e-13
+
+
+def test_periodic_momentum_grows_by_force():
+    rho, ux, uy, uz = W.random_fields(4, 4, 4, seed=4, u_amp=0.03)
+    f = O.init_equilibrium(rho, ux, uy, uz)
+    F = np.array([1e-4, -2e-4, 5e-5])
+    n = 10
+    g = O.run(f, n, bc=0, F=F, omega=O.rates(0.6))
+    e = O.velocity_set().astype(float)
+    p0 = f.reshape(27, -1).sum(axis=1) @ e
+    p1 = g.reshape(27, -1).sum(axis=1) @ e
+    assert np.max(np.abs(p1 - p0 - n * 64 * F)) < 1e-13
+
+
+def _decay_rate(series, t):
+    a = np.log(np.asarray(series))
+    return -np.polyfit(np.asarray(t, float), a, 1)[0]
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.0])
+def test_shear_wave_viscosity(tau):
+    """A transverse wave decays at nu k^2 with nu = cs2 (tau - 1/2) (Eq. transportcoeff3DFPCLBM)."""
+    n = 32
+    rho, ux, uy, uz = W.shear_wave(n, 1e-4)
+    f = O.init_equilibrium(rho, ux, uy, uz)
+    om = O.rates(tau)
+    k = 2 * math.pi / n
+    s = np.sin(k * np.arange(n))
+    amps, ts = [], []
+    t = 0
+    chunk = 20
+    for i in range(16):
+        f = O.run(f, chunk, omega=om)
+        t += chunk
+        if i >= 3:
+            _, u, _, _ = O.moments(f)
+            amps.append(2 / n * np.dot(u[0, :, 0], s))
+            ts.append(t)
+    nu = CS2 * (tau - 0.5)
+    rate = _decay_rate(amps, ts)
+    assert abs(rate / (nu * k * k) - 1) < 0.01
+
+
+def test_sound_wave_attenuation_bulk_viscosity():
+    """A standing acoustic wave rho = 1 + eps sin(ky) loses energy at rate k^2 (4/3 nu + zeta) with
+    zeta = (2/3) cs2 (1/omega_2s - 1/2) (Eq. transportcoeff3DFPCLBM; reading G13 omega_2s = 1)."""
+    n = 32
+    tau = 0.8
+    rho, ux, uy, uz = W.density_wave(n, 1e-5)
+    f = O.init_equilibrium(rho, ux, uy, uz)
+    om = O.rates(tau)
+    k = 2 * math.pi / n
+    y = np.arange(n)
+    s, c = np.sin(k * y), np.cos(k * y)
+    en, ts = [], []
+    t = 0
+    for i in range(60):
+        f = O.run(f, 5, omega=om)
+        t += 5
+        r, _, v, _ = O.moments(f)
+        dr = r[0, :, 0] - 1.0
+        rs, rc = 2 / n * dr @ s, 2 / n * dr @ c
+        vs, vc = 2 / n * v[0, :, 0] @ s, 2 / n * v[0, :, 0] @ c
+        if i >= 4:
+            en.append(CS2 * (rs * rs + rc * rc) + (vs * vs + vc * vc))
+            ts.append(t)
+    nu = CS2 * (tau - 0.5)
+    zeta = 2 / 3 * CS2 * (1 / 1.0 - 0.5)
+    rate = _decay_rate(en, ts)
+    assert abs(rate / (k * k * (4 / 3 * nu + zeta)) - 1) < 0.02
+
+
+def test_taylor_green_low_re_decay():
+    """Low-Re 3D TGV: kinetic energy decays as exp(-6 nu k^2 t) (u0 = 1e-3, 16^3)."""
+    n = 16
+    tau = 0.6
+    rho, ux, uy, uz = W.tgv(n, 1e-3)
+    f = O.init_equilibrium(rho, ux, uy, uz)
+    om = O.rates(tau)
+    k = 2 * math.pi / n
+    ke, ts = [], []
+    t = 0
+    for i in range(8):
+        f = O.run(f, 5, omega=om)
+        t += 5
+        r, a, b, c = O.moments(f)
+        if i >= 2:
+            ke.append(float(np.sum(r * (a * a + b * b + c * c))))
+            ts.append(t)
+    nu = CS2 * (tau - 0.5)
+    rate = _decay_rate(ke, ts)
+    assert abs(rate / (6 * nu * k * k) - 1) < 0.02
+
+
+def test_poiseuille_profile_with_bounce_back():
+    """Body-force channel between half-way bounce-back walls: u(y) = F/(2 rho nu)(y+1/2)(ny-1/2-y)."""
+    ny = 32
+    tau = 0.8
+    nu = CS2 * (tau - 0.5)
+    Fx = 1e-6
+    prof = W.poiseuille_profile(ny, Fx, nu)
+    shape = (1, ny, 1)
+    ux = np.broadcast_to(prof[None, :, None], shape).copy()
+    zero = np.zeros(shape)
+    f = O.init_equilibrium(np.ones(shape), ux, zero, zero)
+    f = O.run(f, 6000, bc=1, F=(Fx, 0, 0), omega=O.rates(tau))
+    _, u, v, _ = O.moments(f, (Fx, 0, 0))
+    err = np.linalg.norm(u[0, :, 0] - prof) / np.linalg.norm(prof)
+    assert err < 0.01
+    assert np.max(np.abs(v)) < 1e-12
