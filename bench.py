@@ -1,0 +1,324 @@
+"""Benchmark of the D3Q27 FPC-LBM fused stream-and-collide step on GB300.
+
+Workload (the metric's configuration): 3D Taylor-Green vortex at Re = 1600 on
+a periodic 256^3 lattice, u0 = 0.05, viscosity from Re, FP32 arithmetic with
+FP32 deviation storage (--precision selects fp16/bf16 storage or fp64).  One
+bench "step" = --inner LBM time steps (one fpclbm_step call).
+
+Reported:
+  value     MLUPS = cells * LBM steps / device time / 1e6, inputs resident in
+            HBM (1.8 GB of populations >> 129 MB L2, so no L2 flush needed)
+  e2e       same metric through the C ABI with host buffers: every bench step
+            copies rho, u from pinned host memory (init_fields), runs --inner
+            steps and reads rho, u back (moments)
+  roofline  step kernel: algorithmic bytes 54 * b per cell update over the
+            measured average launch duration, against MEASURED_PEAKS.json
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the workload
+
+--impl reference times the FP64 CPU oracle (the only reference there is) on a
+bounded sample of the same workload and prints the same JSON line.
+Multi-GPU (torchrun): every rank runs its own box (replicas, weak scaling);
+there is no data exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "D3Q27 FPC-LBM MLUPS & % HBM roofline; closure speedup at stated error"
+BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--precision", default="fp32", choices=list(BYTES))
+    p.add_argument("--inner", type=int, default=64, help="LBM steps per bench step")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--variants", action="store_true", help="also time fp16/bf16 storage")
+    return p.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2410_09739_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision, n):
+    """dram bytes per launch of the step kernel from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    ent = rec.get("entries", {}).get(precision)
+    if not ent:
+        return None
+    return float(ent["bytes_per_cell"]) * n ** 3
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(n, tau, u0, target_s=15.0):
+    """Time the FP64 oracle on a bounded sample of the workload: a 256 x 256 x 1 z-slab of the
+    TGV fields (periodic, one LBM step per repetition) until ~target_s seconds of CPU work."""
+    import oracle as O
+    rho, ux, uy, uz = W.tgv(n, u0)
+    sl = [a[:1].copy() for a in (rho, ux, uy, uz)]
+    f = O.init_equilibrium(*sl)
+    om = O.rates(tau)
+    cells = sl[0].size
+    done, t0 = 0, time.perf_counter()
+    while True:
+        f = O.step(f, omega=om)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            break
+    return {"value": cells * done / el / 1e6, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
+            "sample": "%d x %d x 1 slab of the %d^3 TGV fields, %d FP64 oracle steps, %.1f s" % (
+                n, n, n, done, el)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n, u0 = args.n, 0.05
+    tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
+    import oracle as O
+    rho, ux, uy, uz = W.tgv(n, u0)
+    sl = [a[:1].copy() for a in (rho, ux, uy, uz)]
+    f = O.init_equilibrium(*sl)
+    om = O.rates(tau)
+    cells = sl[0].size
+    for _ in range(args.warmup):
+        f = O.step(f, omega=om)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = O.step(f, omega=om)
+    el = time.perf_counter() - t0
+    v = cells * args.steps / el / 1e6
+    sample = "%d x %d x 1 slab of the %d^3 TGV fields, one FP64 oracle step per bench step" % (n, n, n)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "TGV Re=1600 %d^3 periodic (slab sample)" % n, "precision": "fp64",
+                   "l2": "inputs larger than L2 not applicable (CPU)"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def time_ours(lat, F, torch, args, n, steps, warmup, inner):
+    """Device-resident timing: CUDA events on the library's stream around `steps` fpclbm_step calls."""
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        lat.step(inner)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        lat.step(inner)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_2410_09739_gb300 import fpclbm as F
+    torch.cuda.set_device(local)
+    n, u0 = args.n, 0.05
+    nu = W.tgv_viscosity(n, u0, 1600.0)
+    tau = 3 * nu + 0.5
+    rho, ux, uy, uz = W.tgv(n, u0)
+    ncell = n ** 3
+    stream = torch.cuda.current_stream().cuda_stream
+    results = {}
+    precs = [args.precision] + ([p for p in ("fp16", "bf16") if p != args.precision] if args.variants else [])
+    for prec in precs:
+        lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_PERIODIC, stream=stream)
+        lat.set_params(tau)
+        lat.init_fields(rho, ux, uy, uz)
+        barrier(world)
+        clocks = Clocks(local) if (rank == 0 and prec == args.precision) else None
+        if clocks:
+            clocks.start()
+        el = time_ours(lat, F, torch, args, n, args.steps, args.warmup, args.inner)
+        ck = clocks.stop() if clocks else None
+        el = max_over_ranks(el, world)
+        results[prec] = {"seconds": el, "clocks": ck}
+        if prec == args.precision:
+            # e2e: host buffers through the C ABI, copies inside the timed region
+            hb = [torch.empty(ncell, dtype=torch.float64).pin_memory().numpy() for _ in range(8)]
+            for a, src in zip(hb[:4], (rho, ux, uy, uz)):
+                a[:] = np.asarray(src).reshape(-1)
+            for _ in range(2):
+                F.fpclbm_init_fields(lat.h, *hb[:4], on_device=0)
+                lat.step(args.inner)
+                F.fpclbm_moments(lat.h, *hb[4:], on_device=0)
+            barrier(world)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                F.fpclbm_init_fields(lat.h, *hb[:4], on_device=0)
+                lat.step(args.inner)
+                F.fpclbm_moments(lat.h, *hb[4:], on_device=0)
+            e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+            results[prec]["e2e_s"] = e2e_s
+        lat.close()
+    if rank != 0:
+        return
+    prec = args.precision
+    el = results[prec]["seconds"]
+    lups = ncell * args.inner * args.steps * world
+    value = lups / el / 1e6
+    launches = args.inner * args.steps
+    per_launch = el / launches
+    alg_bytes = 54 * BYTES[prec] * ncell
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / per_launch / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": "TGV Re=1600 %d^3 periodic, u0=0.05, tau=%.6f" % (n, tau), "precision": prec,
+                   "storage": prec, "lbm_steps_per_bench_step": args.inner,
+                   "l2": "inputs larger than L2 (%.2f GB populations)" % (27 * BYTES[prec] * ncell / 1e9),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(prec, n),
+                     "peak_source": peak_kind, "kernel": "fpc::k_step (AA even/odd)",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": ncell * args.inner * args.steps * world / results[prec]["e2e_s"] / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 4 * 8 * ncell, "d2h_bytes_per_step": 4 * 8 * ncell},
+        "gpu_launches": launches,
+        "clocks": results[prec]["clocks"],
+    }
+    if len(results) > 1:
+        out["variants"] = {p: {"MLUPS": ncell * args.inner * args.steps * world / r["seconds"] / 1e6,
+                               "frac_hbm": 54 * BYTES[p] * ncell / (r["seconds"] / launches) / 1e9 / peak}
+                           for p, r in results.items()}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_sample(n, tau, u0)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

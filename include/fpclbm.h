@@ -1,0 +1,180 @@
+/*
+ * fpclbm.h -- C ABI of libfpclbm.so, a GB300 (sm_103a) implementation of the
+ * D3Q27 Fokker-Planck central-moment lattice Boltzmann method (FPC-LBM) of
+ * Schupbach & Premnath, arXiv 2410.09739.
+ *
+ * The library advances the distribution functions f_alpha(x, t) of a D3Q27
+ * lattice (Sec. 3, "Construction of 3D FPC-LBM") by the collide-and-stream
+ * update of Eq. (LBMsteps): per cell, raw moments (Appendix D Step 1), central
+ * moments (Step 2), relaxation of every central moment toward its Markovian
+ * attractor (Eq. Mvcmattractor3D, Step 3) with body-force sources
+ * (Eq. cmupdatesourceD3Q27), back to raw moments and populations (Steps 4, 5)
+ * and streaming (Step 6); density and velocity follow Step 7.
+ *
+ * Conventions shared by every call
+ *   - Lattice units: delta_x = delta_t = 1, cs^2 = 1/3 (Sec. 4).
+ *   - Field arrays are double, x fastest: idx = x + nx*(y + ny*z).  For an
+ *     ensemble the boxes are concatenated in creation order.
+ *   - Population arrays are double, alpha-major: f[alpha*N + idx] with alpha
+ *     in the order of the paper's velocity list (Sec. 3) and N the cell count.
+ *   - Inputs are borrowed for the duration of the call.  Outputs are allocated
+ *     by the caller.  "on_device" = 1 means the pointer is a CUDA device
+ *     pointer on the handle's device; 0 means host memory (pinned or not).
+ *   - The library owns every device allocation it makes; all device work is
+ *     ordered on the stream given at creation (NULL = the legacy default
+ *     stream).  Calls that return data synchronise that stream; fpclbm_step
+ *     synchronises once at its end.
+ *   - A handle must not be used by two host threads at once.
+ *   - Every call returns an FPCLBM_* status; on failure fpclbm_last_error()
+ *     describes it and the handle keeps its previous state unless stated.
+ */
+#ifndef FPCLBM_H
+#define FPCLBM_H
+
+#if defined(__GNUC__)
+#define FPCLBM_API __attribute__((visibility("default")))
+#else
+#define FPCLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fpclbm* fpclbm_t;
+
+/* Status codes. */
+enum {
+    FPCLBM_OK = 0,
+    FPCLBM_ERR_ARG = -1,      /* bad pointer, size or enum value            */
+    FPCLBM_ERR_ALLOC = -2,    /* device or host allocation failed           */
+    FPCLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                 */
+    FPCLBM_ERR_PARAM = -4,    /* a relaxation rate outside (0, 2)           */
+    FPCLBM_ERR_STATE = -5,    /* e.g. step before init_fields               */
+    FPCLBM_ERR_DIVERGED = -6, /* a cell produced rho <= 0, NaN or Inf       */
+    FPCLBM_ERR_TIMEOUT = -7   /* a bounded device wait ran out              */
+};
+
+/* Arithmetic and storage precision of the populations.  Populations are
+ * stored as deviations g = f - w_alpha from the rest state (w = f^eq(1, 0)).
+ * FP64: fp64 storage and arithmetic.  FP32: fp32 storage and arithmetic.
+ * FP32_STORE_FP16 / FP32_STORE_BF16: fp32 arithmetic, 16-bit storage with
+ * round-to-nearest-even. */
+enum { FPCLBM_FP64 = 0, FPCLBM_FP32 = 1, FPCLBM_FP32_STORE_FP16 = 2, FPCLBM_FP32_STORE_BF16 = 3 };
+
+/* Boundaries.  PERIODIC: periodic in x, y, z.  WALLS_Y: stationary half-way
+ * bounce-back walls at y = -1/2 and y = ny - 1/2 (Sec. 4, cubic cavity),
+ * periodic in x and z. */
+enum { FPCLBM_BC_PERIODIC = 0, FPCLBM_BC_WALLS_Y = 1 };
+
+/* Choice of the diffusion tensor D' inside the attractors.
+ * FP: Eq. (diffusion-tensor-parameter-3D): D' = cs^2 delta for order <= 2 and
+ *     D' = kappa~_ij / rho (post-collision second moments) above.
+ * EQUILIBRIUM: D' = cs^2 delta at every order with the lower moments at
+ *     their own attractors, i.e. Maxwellian central moments (the MCM-LBM the
+ *     paper compares with, Sec. 4).
+ * FP_LEARNED: FP plus the learned correction of the shear rates installed by
+ *     fpclbm_set_closure (no counterpart in the paper). */
+enum { FPCLBM_DIFF_FP = 0, FPCLBM_DIFF_EQUILIBRIUM = 1, FPCLBM_DIFF_FP_LEARNED = 2 };
+
+/* Create a single periodic or channel box of nx*ny*nz cells (each >= 1,
+ * product < 2^31).  cuda_stream is a cudaStream_t (NULL allowed).
+ * Parameters start at tau = 1, drift = 0, diffusion = FP, F = 0; the
+ * populations are undefined until fpclbm_init_fields/set_populations.
+ * Errors: ARG, ALLOC, CUDA.  *out is NULL on failure. */
+FPCLBM_API int fpclbm_create(fpclbm_t* out, int nx, int ny, int nz, int precision, int bc, void* cuda_stream);
+
+/* Create an ensemble of n_boxes independent periodic boxes advanced together
+ * by one persistent launch per time step.  dims holds (nx, ny, nz) per box,
+ * tau one shear relaxation time per box (see fpclbm_set_params).  Precision
+ * FP32 only in this version.  Errors: ARG, PARAM, ALLOC, CUDA. */
+FPCLBM_API int fpclbm_create_ensemble(fpclbm_t* out, int n_boxes, const int* dims, const double* tau,
+                           int precision, void* cuda_stream);
+
+/* Initialise every cell to the equilibrium of the given density and velocity:
+ * f = C(u)^-1 kappa^eq(rho, u), kappa^eq the Maxwellian central moments (the
+ * paper gives no initial condition; this is the equilibrium of Sec. 3 at the
+ * given fields).  Resets the step counter to 0.  Errors: ARG, STATE, CUDA. */
+FPCLBM_API int fpclbm_init_fields(fpclbm_t h, const double* rho, const double* ux, const double* uy,
+                       const double* uz, int on_device);
+
+/* Relaxation parameters.  tau: shear relaxation time; omega_4,5,6,8,9 = 1/tau
+ * so that nu = cs^2 (tau - 1/2) (Eq. transportcoeff3DFPCLBM); bulk
+ * omega_7 = 1 (zeta = cs^2/3, Sec. 4); omega_0..3 have no effect and are 1.
+ * drift = omega_FP: rates of orders k >= 3 are k*omega_FP (Sec. 3,
+ * omega_mnp = (m+n+p) omega_FP); drift = 0 selects the paper's experimental
+ * choice of unit rates for all orders >= 3 (Sec. 4).  diffusion: FPCLBM_DIFF_*.
+ * Every resulting rate must lie in (0, 2), else PARAM and nothing changes.
+ * Ensembles: tau scales nothing; per-box tau stays, drift/diffusion apply to
+ * all boxes. */
+FPCLBM_API int fpclbm_set_params(fpclbm_t h, double tau, double drift, int diffusion);
+
+/* Full override of omega_0..omega_26 in the numbering of Appendix D Step 3:
+ * 0:000 1:100 2:010 3:001 4:110 5:101 6:011 7:2s1 8:2d1 9:2d2 10:3s1 11:3m1
+ * 12:3s2 13:3m2 14:3s3 15:3m3 16:111 17:4s1 18:4d1 19:4d2 20:211 21:121
+ * 22:112 23:122 24:212 25:221 26:222.  Rates 4..26 must lie in (0, 2); 0..3
+ * may be any finite value (they cancel).  Single boxes only.  Errors: ARG,
+ * PARAM. */
+FPCLBM_API int fpclbm_set_rates(fpclbm_t h, const double omega[27]);
+
+/* Constant body force per unit volume (F_x, F_y, F_z), Sec. 3
+ * Eq. (forcing:3D); enters as sources sigma_mnp and the half-force velocity
+ * of Step 7.  Errors: ARG (non-finite). */
+FPCLBM_API int fpclbm_set_force(fpclbm_t h, double Fx, double Fy, double Fz);
+
+/* Advance n >= 0 time steps (collide + stream each).  Replays a captured CUDA
+ * graph of the step loop; synchronises the stream once at the end and reads
+ * the divergence flag: DIVERGED if any cell saw rho <= 0, NaN or Inf (the
+ * populations are then whatever the last step wrote).  Errors: ARG, STATE,
+ * CUDA, DIVERGED. */
+FPCLBM_API int fpclbm_step(fpclbm_t h, long long n);
+
+/* Density and half-force velocity of every cell (Appendix D Step 7:
+ * rho = sum f, rho u = sum f e + F/2).  Outputs of N doubles each; any of the
+ * four pointers may be NULL to skip it.  Errors: ARG, STATE, CUDA. */
+FPCLBM_API int fpclbm_moments(fpclbm_t h, double* rho, double* ux, double* uy, double* uz, int on_device);
+
+/* Global diagnostics reduced in fp64 on the device: out[0] = sum rho,
+ * out[1..3] = sum rho u (Step 7 velocity), out[4] = sum rho |u|^2 / 2.
+ * Deterministic (fixed reduction order).  out is host memory.
+ * Errors: ARG, STATE, CUDA. */
+FPCLBM_API int fpclbm_diagnostics(fpclbm_t h, double out[5]);
+
+/* Copy out / in all populations as full f (not deviations), double,
+ * alpha-major in the paper's alpha order, host memory.  get works at any
+ * step parity; set leaves the handle at step 0 of a new run.
+ * Errors: ARG, STATE (get before init), CUDA. */
+FPCLBM_API int fpclbm_get_populations(fpclbm_t h, double* f);
+FPCLBM_API int fpclbm_set_populations(fpclbm_t h, const double* f);
+
+/* Populations (full f, double) of the n listed cells only: f[alpha * n + i] for
+ * cell index cells[i] (0 <= cells[i] < N), paper alpha order, host memory.
+ * For checking single cells of large runs and for probes.  Errors: ARG,
+ * STATE, CUDA. */
+FPCLBM_API int fpclbm_get_populations_at(fpclbm_t h, const long long* cells, int n, double* f);
+
+/* Steps taken since the last init_fields / set_populations. */
+FPCLBM_API int fpclbm_get_step_count(fpclbm_t h, long long* steps);
+
+/* Install the learned closure used by FPCLBM_DIFF_FP_LEARNED: a per-cell
+ * MLP 9 -> 64 -> 64 -> 1 (tanh hidden layers) whose inputs are the six
+ * non-equilibrium second-order central moments and u, and whose output is
+ * added to the shear rates omega_4,5,6,8,9 (clamped to (0, 2)).  Weights are
+ * bf16 bit patterns, n_params = 4865, in the order W1[64][9], b1[64],
+ * W2[64][64], b2[64], W3[1][64], b3[1] (row-major, out x in).  No
+ * counterpart in the paper, whose channel uses a Smagorinsky LES (Sec. 4).
+ * Errors: ARG. */
+FPCLBM_API int fpclbm_set_closure(fpclbm_t h, const unsigned short* bf16_weights, int n_params);
+
+/* Release everything the handle owns.  NULL is a no-op.  Returns OK. */
+FPCLBM_API int fpclbm_destroy(fpclbm_t h);
+
+/* Text of the last error on this handle ("" if none); owned by the handle
+ * and valid until its next call.  With h = NULL: the last error of a failed
+ * fpclbm_create / fpclbm_create_ensemble on this thread. */
+FPCLBM_API const char* fpclbm_last_error(fpclbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPCLBM_H */

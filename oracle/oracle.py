@@ -19,7 +19,7 @@ from . import build as _build
 __all__ = [
     "lib", "velocity_set", "moment_exponents", "central_matrix", "grouping_matrix",
     "attractor_generic", "maxwell_moments", "collide", "equilibrium", "init_equilibrium",
-    "step", "run", "moments", "rates", "EQ_MODE_FP", "EQ_MODE_MCM",
+    "step", "run", "moments", "rates", "threads", "EQ_MODE_FP", "EQ_MODE_MCM",
 ]
 
 EQ_MODE_FP = 0   # diffusion tensor of Eq. (diffusion-tensor-parameter-3D)

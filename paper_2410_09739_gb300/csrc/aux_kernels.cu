@@ -1,0 +1,298 @@
+// aux_kernels.cu -- initialisation, field export, population I/O and fp64
+// diagnostics of one box.  None of these is on the time-step hot path; they
+// compute in fp64 whatever the storage precision.
+#include "internal.h"
+
+namespace fpc {
+
+// Velocity list of the paper (Sec. 3, D3Q27), alpha = 0..26, and the tensor
+// slot (ex+1) + 3 (ey+1) + 9 (ez+1) of each alpha.
+static const int kEx[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+static const int kEy[27] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
+static const int kEz[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
+
+#define FPC_SLOT(a) ((kEx[a] + 1) + 3 * (kEy[a] + 1) + 9 * (kEz[a] + 1))
+const int kSlotOfAlpha[27] = {FPC_SLOT(0),  FPC_SLOT(1),  FPC_SLOT(2),  FPC_SLOT(3),  FPC_SLOT(4),  FPC_SLOT(5),
+                              FPC_SLOT(6),  FPC_SLOT(7),  FPC_SLOT(8),  FPC_SLOT(9),  FPC_SLOT(10), FPC_SLOT(11),
+                              FPC_SLOT(12), FPC_SLOT(13), FPC_SLOT(14), FPC_SLOT(15), FPC_SLOT(16), FPC_SLOT(17),
+                              FPC_SLOT(18), FPC_SLOT(19), FPC_SLOT(20), FPC_SLOT(21), FPC_SLOT(22), FPC_SLOT(23),
+                              FPC_SLOT(24), FPC_SLOT(25), FPC_SLOT(26)};
+#undef FPC_SLOT
+
+struct AlphaMap {
+    int slot[27];
+};
+
+static AlphaMap alpha_map()
+{
+    AlphaMap m;
+    for (int a = 0; a < 27; ++a) m.slot[a] = kSlotOfAlpha[a];
+    return m;
+}
+
+__device__ __forceinline__ void cell_xyz(const BoxGeom& b, unsigned cell, unsigned& x, unsigned& y, unsigned& z)
+{
+    z = fdiv(cell, b.div_nxny);
+    const unsigned rem = cell - z * (unsigned)(b.nx * b.ny);
+    y = fdiv(rem, b.div_nx);
+    x = rem - y * b.nx;
+}
+
+// Deviations g_s(x) at the current time, whatever the AA parity.
+// parity 0: buf[s][x]; parity 1: buf[26-s][x - e_s], or buf[s][x] when the
+// source lies in a y wall (see step_kernels.cu).
+template <typename S>
+__device__ void load_cell(const BoxGeom& b, int parity, unsigned cell, double g[27])
+{
+    const S* buf = static_cast<const S*>(b.buf);
+    if (parity == 0) {
+        for (int s = 0; s < 27; ++s) g[s] = Store<S>::ldd(buf + (size_t)s * b.stride + cell);
+        return;
+    }
+    unsigned x, y, z;
+    cell_xyz(b, cell, x, y, z);
+    const int nx = b.nx, ny = b.ny, nz = b.nz;
+    for (int s = 0; s < 27; ++s) {
+        const int ex = s % 3 - 1, ey = (s / 3) % 3 - 1, ez = s / 9 - 1;
+        const int sy = (int)y - ey;
+        if (b.walls && (sy < 0 || sy >= ny)) {
+            g[s] = Store<S>::ldd(buf + (size_t)s * b.stride + cell);
+            continue;
+        }
+        const int sx = ((int)x - ex + nx) % nx, syw = (sy + ny) % ny, sz = ((int)z - ez + nz) % nz;
+        const size_t src = (size_t)sx + (size_t)nx * ((size_t)syw + (size_t)ny * sz);
+        g[s] = Store<S>::ldd(buf + (size_t)(26 - s) * b.stride + src);
+    }
+}
+
+// Equilibrium deviation f^eq(rho, u) - w in product form: per axis
+// phi(0) = 2/3 - u^2, phi(+-1) = 1/6 + (u^2 +- u)/2, i.e. w1 + dphi; the
+// product (w1x + ax)(w1y + ay)(w1z + az) - w1x w1y w1z is expanded so that
+// only small terms are summed.  (Equal to C(u)^-1 kappa^eq with kappa^eq the
+// Maxwellian central moments (1, 0, cs^2) per axis.)
+template <typename S>
+__global__ void k_init_eq(BoxGeom b, const double* rho, const double* ux, const double* uy, const double* uz,
+                          unsigned c0, unsigned n)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned cell = c0 + i;
+    const double r = rho[i], u[3] = {ux[i], uy[i], uz[i]};
+    double dphi[3][3];
+    for (int d = 0; d < 3; ++d) {
+        const double v = u[d], v2 = v * v;
+        dphi[d][0] = 0.5 * (v2 - v);
+        dphi[d][1] = -v2;
+        dphi[d][2] = 0.5 * (v2 + v);
+    }
+    S* buf = static_cast<S*>(b.buf);
+    for (int s = 0; s < 27; ++s) {
+        const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
+        const double A = w1(ix), B = w1(iy), C = w1(iz);
+        const double a = dphi[0][ix], bb = dphi[1][iy], c = dphi[2][iz];
+        // (A+a)(B+bb)(C+c) - ABC
+        const double dprod = a * (B + bb) * (C + c) + A * (bb * (C + c) + B * c);
+        const double feq_dev = (r - 1.0) * ((A + a) * (B + bb) * (C + c)) + dprod;
+        buf[(size_t)s * b.stride + cell] = Store<S>::fromd(feq_dev);
+    }
+}
+
+template <typename S>
+__global__ void k_moments(BoxGeom b, int parity, double Fx, double Fy, double Fz, double* rho, double* ux,
+                          double* uy, double* uz, unsigned c0, unsigned n)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double g[27];
+    load_cell<S>(b, parity, c0 + i, g);
+    double dr = 0, jx = 0, jy = 0, jz = 0;
+    for (int s = 0; s < 27; ++s) {
+        dr += g[s];
+        jx += (s % 3 - 1) * g[s];
+        jy += ((s / 3) % 3 - 1) * g[s];
+        jz += (s / 9 - 1) * g[s];
+    }
+    const double r = 1.0 + dr;
+    if (rho) rho[i] = r;
+    if (ux) ux[i] = (jx + 0.5 * Fx) / r;
+    if (uy) uy[i] = (jy + 0.5 * Fy) / r;
+    if (uz) uz[i] = (jz + 0.5 * Fz) / r;
+}
+
+template <typename S>
+__global__ void k_get_pops(BoxGeom b, AlphaMap am, int parity, double* out, unsigned ld, unsigned c0, unsigned n)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double g[27];
+    load_cell<S>(b, parity, c0 + i, g);
+    for (int a = 0; a < 27; ++a) {
+        const int s = am.slot[a];
+        out[(size_t)a * ld + i] = wslot(s) + g[s];
+    }
+}
+
+template <typename S>
+__global__ void k_get_pops_at(BoxGeom b, AlphaMap am, int parity, const unsigned* cells, unsigned n, double* out)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned cell = cells[i];
+    if (cell >= b.ncells) return;
+    double g[27];
+    load_cell<S>(b, parity, cell, g);
+    for (int a = 0; a < 27; ++a) {
+        const int s = am.slot[a];
+        out[(size_t)a * n + i] = wslot(s) + g[s];
+    }
+}
+
+template <typename S>
+__global__ void k_set_pops(BoxGeom b, AlphaMap am, const double* in, unsigned ld, unsigned c0, unsigned n)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    S* buf = static_cast<S*>(b.buf);
+    for (int a = 0; a < 27; ++a) {
+        const int s = am.slot[a];
+        buf[(size_t)s * b.stride + c0 + i] = Store<S>::fromd(in[(size_t)a * ld + i] - wslot(s));
+    }
+}
+
+// Diagnostics: per-block sums of (rho, rho u, rho |u|^2 / 2) in fp64 with a
+// fixed tree order, then one block sums the partials in index order.
+constexpr int kDiagThreads = 256;
+
+int diag_blocks(unsigned ncells)
+{
+    const unsigned per = kDiagThreads * 8u;
+    unsigned nb = (ncells + per - 1) / per;
+    return (int)(nb < 1 ? 1 : nb);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(BoxGeom b, int parity, double Fx, double Fy,
+                                                               double Fz, double* part)
+{
+    __shared__ double sh[5][kDiagThreads];
+    double acc[5] = {0, 0, 0, 0, 0};
+    const unsigned base = blockIdx.x * kDiagThreads * 8u;
+    for (int k = 0; k < 8; ++k) {
+        const unsigned cell = base + k * kDiagThreads + threadIdx.x;
+        if (cell >= b.ncells) break;
+        double g[27];
+        load_cell<S>(b, parity, cell, g);
+        double dr = 0, jx = 0, jy = 0, jz = 0;
+        for (int s = 0; s < 27; ++s) {
+            dr += g[s];
+            jx += (s % 3 - 1) * g[s];
+            jy += ((s / 3) % 3 - 1) * g[s];
+            jz += (s / 9 - 1) * g[s];
+        }
+        const double r = 1.0 + dr;
+        const double mx = jx + 0.5 * Fx, my = jy + 0.5 * Fy, mz = jz + 0.5 * Fz;  // rho u
+        acc[0] += r;
+        acc[1] += mx;
+        acc[2] += my;
+        acc[3] += mz;
+        acc[4] += 0.5 * (mx * mx + my * my + mz * mz) / r;
+    }
+    for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < (unsigned)w)
+            for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 5; ++q) part[(size_t)5 * blockIdx.x + q] = sh[q][0];
+}
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* part, int nblocks, double* out)
+{
+    __shared__ double sh[5][kDiagThreads];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < nblocks; i += kDiagThreads)
+        for (int q = 0; q < 5; ++q) acc[q] += part[(size_t)5 * i + q];
+    for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < (unsigned)w)
+            for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 5; ++q) out[q] = sh[q][0];
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+
+#define FPC_DISPATCH(prec, KCALL)                                   \
+    switch (prec) {                                                 \
+        case P_FP64: { using S = double; KCALL; break; }            \
+        case P_FP32: { using S = float; KCALL; break; }             \
+        case P_FP16: { using S = __half; KCALL; break; }            \
+        case P_BF16: { using S = __nv_bfloat16; KCALL; break; }     \
+        default: return cudaErrorInvalidValue;                      \
+    }
+
+static inline unsigned blocks_for(unsigned n, int t) { return (n + t - 1) / t; }
+
+cudaError_t launch_init_eq(int precision, const BoxGeom& b, const double* rho, const double* ux, const double* uy,
+                           const double* uz, unsigned c0, unsigned n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    FPC_DISPATCH(precision, (k_init_eq<S><<<blocks_for(n, 256), 256, 0, st>>>(b, rho, ux, uy, uz, c0, n)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int precision, const BoxGeom& b, int parity, double Fx, double Fy, double Fz, double* rho,
+                           double* ux, double* uy, double* uz, unsigned c0, unsigned n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    FPC_DISPATCH(precision,
+                 (k_moments<S><<<blocks_for(n, 256), 256, 0, st>>>(b, parity, Fx, Fy, Fz, rho, ux, uy, uz, c0, n)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_pops(int precision, const BoxGeom& b, int parity, double* out, unsigned ld, unsigned c0,
+                            unsigned n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const AlphaMap am = alpha_map();
+    FPC_DISPATCH(precision, (k_get_pops<S><<<blocks_for(n, 128), 128, 0, st>>>(b, am, parity, out, ld, c0, n)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_pops_at(int precision, const BoxGeom& b, int parity, const unsigned* cells, unsigned n,
+                               double* out, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const AlphaMap am = alpha_map();
+    FPC_DISPATCH(precision, (k_get_pops_at<S><<<blocks_for(n, 128), 128, 0, st>>>(b, am, parity, cells, n, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_pops(int precision, const BoxGeom& b, const double* in, unsigned ld, unsigned c0, unsigned n,
+                            cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const AlphaMap am = alpha_map();
+    FPC_DISPATCH(precision, (k_set_pops<S><<<blocks_for(n, 128), 128, 0, st>>>(b, am, in, ld, c0, n)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(int precision, const BoxGeom& b, int parity, double Fx, double Fy, double Fz,
+                               double* part, double* out, cudaStream_t st)
+{
+    const int nb = diag_blocks(b.ncells);
+    FPC_DISPATCH(precision, (k_diag_partial<S><<<nb, kDiagThreads, 0, st>>>(b, parity, Fx, Fy, Fz, part)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_diag_final<<<1, kDiagThreads, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fpc

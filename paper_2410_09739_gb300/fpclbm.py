@@ -1,0 +1,297 @@
+"""Thin ctypes binding of libfpclbm.so (include/fpclbm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The module-level functions carry the C names; ``Lattice`` is a
+small convenience wrapper over them.  There is no CPU fallback: if the shared
+library is missing or fails to load, every call raises.
+
+Arrays passed to the library are float64.  Host arrays may be numpy arrays or
+CPU torch tensors; device arrays (``on_device=1``) must be CUDA torch tensors
+on the handle's device.  Field arrays are shaped [nz, ny, nx] (x fastest) or
+flat; population arrays are [27, N] in the paper's alpha order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfpclbm.so")
+
+FPCLBM_OK = 0
+FPCLBM_ERR_ARG = -1
+FPCLBM_ERR_ALLOC = -2
+FPCLBM_ERR_CUDA = -3
+FPCLBM_ERR_PARAM = -4
+FPCLBM_ERR_STATE = -5
+FPCLBM_ERR_DIVERGED = -6
+FPCLBM_ERR_TIMEOUT = -7
+
+FPCLBM_FP64 = 0
+FPCLBM_FP32 = 1
+FPCLBM_FP32_STORE_FP16 = 2
+FPCLBM_FP32_STORE_BF16 = 3
+
+FPCLBM_BC_PERIODIC = 0
+FPCLBM_BC_WALLS_Y = 1
+
+FPCLBM_DIFF_FP = 0
+FPCLBM_DIFF_EQUILIBRIUM = 1
+FPCLBM_DIFF_FP_LEARNED = 2
+
+PRECISIONS = {"fp64": FPCLBM_FP64, "fp32": FPCLBM_FP32, "fp16": FPCLBM_FP32_STORE_FP16,
+              "bf16": FPCLBM_FP32_STORE_BF16}
+
+EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fpclbm_set_params",
+            "fpclbm_set_rates", "fpclbm_set_force", "fpclbm_step", "fpclbm_moments", "fpclbm_diagnostics",
+            "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_set_closure",
+            "fpclbm_destroy", "fpclbm_last_error")
+
+
+class FpclbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("fpclbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: str = LIB_PATH):
+    """Load libfpclbm.so (no fallback: raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError("libfpclbm.so not built: %s (run __graft_entry__.build())" % path)
+    L = ctypes.CDLL(path)
+    L.fpclbm_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, _P]
+    L.fpclbm_create_ensemble.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D,
+                                         ctypes.c_int, _P]
+    L.fpclbm_init_fields.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int]
+    L.fpclbm_set_params.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.fpclbm_set_rates.argtypes = [_P, _D]
+    L.fpclbm_set_force.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.fpclbm_step.argtypes = [_P, ctypes.c_longlong]
+    L.fpclbm_moments.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int]
+    L.fpclbm_diagnostics.argtypes = [_P, _D]
+    L.fpclbm_get_populations.argtypes = [_P, _P]
+    L.fpclbm_get_populations_at.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, _P]
+    L.fpclbm_set_populations.argtypes = [_P, _P]
+    L.fpclbm_get_step_count.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong)]
+    L.fpclbm_set_closure.argtypes = [_P, ctypes.POINTER(ctypes.c_ushort), ctypes.c_int]
+    L.fpclbm_destroy.argtypes = [_P]
+    L.fpclbm_last_error.argtypes = [_P]
+    L.fpclbm_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "fpclbm_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(h, rc: int):
+    if rc != FPCLBM_OK:
+        msg = load().fpclbm_last_error(h)
+        raise FpclbmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a, on_device: bool):
+    """Raw data pointer of a float64 array (numpy, or torch CPU/CUDA tensor)."""
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise TypeError("tensor must be contiguous float64")
+            if a.is_cuda != bool(on_device):
+                raise TypeError("tensor device does not match on_device=%d" % on_device)
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:  # pragma: no cover
+        pass
+    if on_device:
+        raise TypeError("on_device=1 needs a CUDA torch tensor")
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("host arrays must be C-contiguous float64 numpy arrays")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# --- functions with the C names ---------------------------------------------------------
+
+def fpclbm_create(nx: int, ny: int, nz: int, precision: int, bc: int = FPCLBM_BC_PERIODIC, stream: int = 0):
+    h = _P()
+    rc = load().fpclbm_create(ctypes.byref(h), nx, ny, nz, precision, bc, _P(stream) if stream else None)
+    _check(None, rc)
+    return h
+
+
+def fpclbm_create_ensemble(dims, tau, precision: int = FPCLBM_FP32, stream: int = 0):
+    dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1))
+    tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64).reshape(-1))
+    h = _P()
+    rc = load().fpclbm_create_ensemble(ctypes.byref(h), len(tau), dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                       tau.ctypes.data_as(_D), precision, _P(stream) if stream else None)
+    _check(None, rc)
+    return h
+
+
+def fpclbm_init_fields(h, rho, ux, uy, uz, on_device: int = 0):
+    return _check(h, load().fpclbm_init_fields(h, *(_ptr(a, on_device) for a in (rho, ux, uy, uz)), on_device))
+
+
+def fpclbm_set_params(h, tau: float, drift: float = 0.0, diffusion: int = FPCLBM_DIFF_FP):
+    return _check(h, load().fpclbm_set_params(h, float(tau), float(drift), int(diffusion)))
+
+
+def fpclbm_set_rates(h, omega):
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    assert om.size == 27
+    return _check(h, load().fpclbm_set_rates(h, om.ctypes.data_as(_D)))
+
+
+def fpclbm_set_force(h, Fx: float, Fy: float, Fz: float):
+    return _check(h, load().fpclbm_set_force(h, float(Fx), float(Fy), float(Fz)))
+
+
+def fpclbm_step(h, n: int):
+    return _check(h, load().fpclbm_step(h, int(n)))
+
+
+def fpclbm_moments(h, rho, ux, uy, uz, on_device: int = 0):
+    return _check(h, load().fpclbm_moments(h, *(_ptr(a, on_device) for a in (rho, ux, uy, uz)), on_device))
+
+
+def fpclbm_diagnostics(h) -> np.ndarray:
+    out = np.zeros(5)
+    _check(h, load().fpclbm_diagnostics(h, out.ctypes.data_as(_D)))
+    return out
+
+
+def fpclbm_get_populations(h, f):
+    return _check(h, load().fpclbm_get_populations(h, _ptr(f, 0)))
+
+
+def fpclbm_get_populations_at(h, cells) -> np.ndarray:
+    """Populations [27, n] of the listed flat cell indices."""
+    c = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+    out = np.empty((27, c.size))
+    _check(h, load().fpclbm_get_populations_at(h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), c.size,
+                                               _ptr(out, 0)))
+    return out
+
+
+def fpclbm_set_populations(h, f):
+    return _check(h, load().fpclbm_set_populations(h, _ptr(f, 0)))
+
+
+def fpclbm_get_step_count(h) -> int:
+    v = ctypes.c_longlong()
+    _check(h, load().fpclbm_get_step_count(h, ctypes.byref(v)))
+    return v.value
+
+
+def fpclbm_set_closure(h, bf16_bits):
+    w = np.ascontiguousarray(np.asarray(bf16_bits, dtype=np.uint16))
+    return _check(h, load().fpclbm_set_closure(h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_ushort)), w.size))
+
+
+def fpclbm_destroy(h):
+    return load().fpclbm_destroy(h)
+
+
+def fpclbm_last_error(h) -> str:
+    m = load().fpclbm_last_error(h)
+    return m.decode() if m else ""
+
+
+# --- convenience wrapper ------------------------------------------------------------------
+
+class Lattice:
+    """One box (or ensemble) handle; methods map 1:1 onto the C calls."""
+
+    def __init__(self, nx: int, ny: int, nz: int, precision="fp32", bc: int = FPCLBM_BC_PERIODIC, stream: int = 0):
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.shape = (nz, ny, nx)
+        self.ncells = nx * ny * nz
+        self.h = fpclbm_create(nx, ny, nz, self.precision, bc, stream)
+
+    @classmethod
+    def ensemble(cls, dims, tau, precision="fp32", stream: int = 0):
+        self = cls.__new__(cls)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d = np.asarray(dims, dtype=np.int64).reshape(-1, 3)
+        self.shape = None
+        self.ncells = int(np.sum(np.prod(d, axis=1)))
+        self.h = fpclbm_create_ensemble(d, tau, self.precision, stream)
+        return self
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            fpclbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _f64(a):
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+
+    def init_fields(self, rho, ux, uy, uz):
+        arrs = [self._f64(a) for a in (rho, ux, uy, uz)]
+        return fpclbm_init_fields(self.h, *arrs, on_device=0)
+
+    def set_params(self, tau, drift=0.0, diffusion=FPCLBM_DIFF_FP):
+        return fpclbm_set_params(self.h, tau, drift, diffusion)
+
+    def set_rates(self, omega):
+        return fpclbm_set_rates(self.h, omega)
+
+    def set_force(self, Fx, Fy=0.0, Fz=0.0):
+        return fpclbm_set_force(self.h, Fx, Fy, Fz)
+
+    def step(self, n: int = 1):
+        return fpclbm_step(self.h, n)
+
+    def moments(self):
+        outs = [np.empty(self.ncells) for _ in range(4)]
+        fpclbm_moments(self.h, *outs, on_device=0)
+        if self.shape is not None:
+            outs = [o.reshape(self.shape) for o in outs]
+        return tuple(outs)
+
+    def diagnostics(self):
+        return fpclbm_diagnostics(self.h)
+
+    def get_populations(self):
+        f = np.empty((27, self.ncells))
+        fpclbm_get_populations(self.h, f)
+        return f.reshape((27,) + self.shape) if self.shape is not None else f
+
+    def set_populations(self, f):
+        return fpclbm_set_populations(self.h, self._f64(f))
+
+    def populations_at(self, cells):
+        return fpclbm_get_populations_at(self.h, cells)
+
+    def step_count(self) -> int:
+        return fpclbm_get_step_count(self.h)
+
+    def set_closure(self, bf16_bits):
+        return fpclbm_set_closure(self.h, bf16_bits)

@@ -1,0 +1,327 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (written per test, derived from the arithmetic):
+  * FP64 path: max |f_gpu - f_oracle| <= 1e-12 * max |f| per step (the stated
+    bound); both sides are fp64, so the gap is rounding order only.
+  * FP32 path: every operation rounds at 2^-24 relative to values that are
+    deviations from the rest state (|g| <~ 0.1 here); a bound of 1e-6
+    absolute per step on f covers ~100 such roundings with margin.
+  * 16-bit storage: the oracle starts from the GPU's own rounded populations
+    (read back exactly), so one step differs by the final rounding of the
+    deviation, <= 2^-11 |g~| (fp16) or 2^-8 |g~| (bf16), plus the fp32 term.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle_local import LocalOracle
+from paper_2410_09739_gb300 import fpclbm as F
+
+pytestmark = pytest.mark.gpu
+
+W_REST = O.equilibrium(1.0, [0, 0, 0])
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def near_eq_populations(nx, ny, nz, seed, u_amp=0.05, noise=0.02):
+    """Equilibrium of random fields plus a random non-equilibrium part (host, oracle side)."""
+    rho, ux, uy, uz = W.random_fields(nx, ny, nz, seed, u_amp=u_amp)
+    f = O.init_equilibrium(rho, ux, uy, uz)
+    rng = np.random.default_rng(seed + 1000)
+    return f * (1.0 + noise * rng.uniform(-1, 1, f.shape))
+
+
+def random_rates(seed):
+    rng = np.random.default_rng(seed)
+    om = rng.uniform(0.4, 1.8, 27)
+    om[:4] = rng.uniform(-1, 3, 4)  # no effect on the result
+    return om
+
+
+def make(nx, ny, nz, prec, bc=0, F_=(0, 0, 0), omega=None, tau=None, drift=0.0, mode=0):
+    lat = F.Lattice(nx, ny, nz, prec, bc)
+    if omega is not None:
+        lat.set_params(1.0, 0.0, mode)
+        lat.set_rates(omega)
+    else:
+        lat.set_params(tau if tau is not None else 0.8, drift, mode)
+    lat.set_force(*F_)
+    return lat
+
+
+SHAPES = [(1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 4, 4), (5, 4, 3), (17, 9, 5), (33, 7, 6)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_init_matches_oracle_equilibrium(shape):
+    nx, ny, nz = shape
+    rho, ux, uy, uz = W.random_fields(nx, ny, nz, seed=5, u_amp=0.1)
+    with make(nx, ny, nz, "fp64") as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        got = lat.get_populations()
+    assert rel(got, O.init_equilibrium(rho, ux, uy, uz)) < 1e-14
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("force", [False, True])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_one_step_fp64_random_populations(shape, bc, force, mode):
+    nx, ny, nz = shape
+    seed = nx * 1000 + ny * 100 + nz * 10 + bc * 7 + force * 3 + mode
+    f0 = W.random_populations(nx * ny * nz, seed).reshape(27, nz, ny, nx)
+    Fv = (2e-3, -1e-3, 1.5e-3) if force else (0, 0, 0)
+    om = random_rates(seed)
+    with make(nx, ny, nz, "fp64", bc, Fv, omega=om, mode=mode) as lat:
+        lat.set_populations(f0)
+        lat.step(1)
+        got = lat.get_populations()
+    ref = O.step(f0, bc=bc, F=Fv, omega=om, mode=mode)
+    assert rel(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("nsteps", [2, 3, 10, 33, 70])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_multi_step_fp64(nsteps, bc):
+    """Covers both AA parities, the odd-count readback and the captured graph (>= 32 steps)."""
+    nx, ny, nz = 17, 9, 5
+    f0 = near_eq_populations(nx, ny, nz, seed=nsteps)
+    Fv = (1e-4, 2e-5, -3e-5)
+    om = O.rates(0.7, 0.3)
+    with make(nx, ny, nz, "fp64", bc, Fv, tau=0.7, drift=0.3) as lat:
+        lat.set_populations(f0)
+        lat.step(nsteps)
+        got = lat.get_populations()
+        assert lat.step_count() == nsteps
+    ref = O.run(f0, nsteps, bc=bc, F=Fv, omega=om)
+    assert rel(got, ref) <= 1e-12 * nsteps
+
+
+def test_split_step_calls_equal_one_call():
+    nx, ny, nz = 9, 6, 5
+    f0 = near_eq_populations(nx, ny, nz, seed=3)
+    with make(nx, ny, nz, "fp64", 1, (1e-4, 0, 0), tau=0.6) as a, make(nx, ny, nz, "fp64", 1, (1e-4, 0, 0),
+                                                                        tau=0.6) as b:
+        a.set_populations(f0)
+        b.set_populations(f0)
+        a.step(77)
+        for n in (1, 2, 33, 5, 36):
+            b.step(n)
+        assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+def test_tgv_32_fp64_200_steps_matches_oracle():
+    """Config: 3D Taylor-Green vortex, FP64, periodic 32^3, rho = 1, u0 = 0.05, tau = 0.6, 200 steps."""
+    n, u0, tau, steps = 32, 0.05, 0.6, 200
+    rho, ux, uy, uz = W.tgv(n, u0)
+    with make(n, n, n, "fp64", tau=tau) as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        lat.step(steps)
+        got = lat.get_populations()
+        r, a, b, c = lat.moments()
+    ref = O.run(O.init_equilibrium(rho, ux, uy, uz), steps, omega=O.rates(tau))
+    assert rel(got, ref) <= 1e-10
+    # kinetic energy against the low-Re decay exp(-6 nu k^2 t); at u0 = 0.05 (Re ~ 7.6) the
+    # nonlinear transfer keeps it within a few percent, not exact
+    nu = (tau - 0.5) / 3.0
+    k = 2 * math.pi / n
+    r0, a0, b0, c0 = (np.asarray(v) for v in (rho, ux, uy, uz))
+    ke0 = np.sum(r0 * (a0 ** 2 + b0 ** 2 + c0 ** 2))
+    ke = np.sum(r * (a * a + b * b + c * c))
+    assert abs(ke / ke0 / math.exp(-6 * nu * k * k * steps) - 1) < 0.05
+
+
+@pytest.mark.parametrize("prec,unit", [("fp32", 0.0), ("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_one_step_reduced_precision(prec, unit, bc):
+    nx, ny, nz = 17, 9, 5
+    f0 = near_eq_populations(nx, ny, nz, seed=11)
+    Fv = (1e-4, 0, 5e-5)
+    om = O.rates(0.6)
+    with make(nx, ny, nz, prec, bc, Fv, tau=0.6) as lat:
+        lat.set_populations(f0)
+        fq = lat.get_populations()  # the stored (rounded) state, exactly
+        lat.step(1)
+        got = lat.get_populations()
+    ref = O.step(fq, bc=bc, F=Fv, omega=om)
+    w = W_REST[:, None, None, None]
+    bound = unit * np.abs(ref - w) + 1e-6
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_moments_and_diagnostics_fp64():
+    nx, ny, nz = 17, 9, 5
+    f0 = near_eq_populations(nx, ny, nz, seed=21)
+    Fv = (1e-4, -5e-5, 0)
+    with make(nx, ny, nz, "fp64", 1, Fv, tau=0.9) as lat:
+        lat.set_populations(f0)
+        lat.step(5)
+        r, a, b, c = lat.moments()
+        d = lat.diagnostics()
+    ref = O.run(f0, 5, bc=1, F=Fv, omega=O.rates(0.9))
+    R, A, B, C = O.moments(ref, Fv)
+    for x, y in ((r, R), (a, A), (b, B), (c, C)):
+        assert np.max(np.abs(x - y)) < 1e-13
+    expect = [R.sum(), (R * A).sum(), (R * B).sum(), (R * C).sum(), 0.5 * (R * (A * A + B * B + C * C)).sum()]
+    assert np.allclose(d, expect, rtol=1e-13, atol=1e-16)
+
+
+def test_moments_on_device_match_host():
+    torch = pytest.importorskip("torch")
+    nx, ny, nz = 17, 9, 5
+    rho, ux, uy, uz = W.random_fields(nx, ny, nz, seed=8)
+    with make(nx, ny, nz, "fp32", tau=0.7) as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        lat.step(3)
+        host = lat.moments()
+        dev = [torch.empty(nx * ny * nz, dtype=torch.float64, device="cuda") for _ in range(4)]
+        F.fpclbm_moments(lat.h, *dev, on_device=1)
+        torch.cuda.synchronize()
+        for h_, d_ in zip(host, dev):
+            assert np.array_equal(h_.reshape(-1), d_.cpu().numpy())
+        # device-side init from torch tensors gives the same state as host init
+        t = [torch.tensor(np.ascontiguousarray(v).reshape(-1), device="cuda") for v in (rho, ux, uy, uz)]
+        F.fpclbm_init_fields(lat.h, *t, on_device=1)
+        a = lat.get_populations()
+        lat.init_fields(rho, ux, uy, uz)
+        assert np.array_equal(a, lat.get_populations())
+
+
+def test_divergence_is_reported():
+    nx, ny, nz = 8, 8, 8
+    f0 = near_eq_populations(nx, ny, nz, seed=2)
+    f0[:, 3, 4, 5] = np.nan
+    with make(nx, ny, nz, "fp32", tau=0.7) as lat:
+        lat.set_populations(f0)
+        with pytest.raises(F.FpclbmError) as e:
+            lat.step(4)
+        assert e.value.code == F.FPCLBM_ERR_DIVERGED
+    f0 = near_eq_populations(nx, ny, nz, seed=2)
+    f0[:, 1, 1, 1] = -0.1  # negative density
+    with make(nx, ny, nz, "fp32", tau=0.7) as lat:
+        lat.set_populations(f0)
+        with pytest.raises(F.FpclbmError) as e:
+            lat.step(1)
+        assert e.value.code == F.FPCLBM_ERR_DIVERGED
+
+
+def test_parameter_and_state_errors():
+    with F.Lattice(4, 4, 4, "fp32") as lat:
+        with pytest.raises(F.FpclbmError) as e:
+            lat.step(1)
+        assert e.value.code == F.FPCLBM_ERR_STATE
+        with pytest.raises(F.FpclbmError) as e:
+            lat.set_params(0.45)  # omega = 2.22
+        assert e.value.code == F.FPCLBM_ERR_PARAM
+        with pytest.raises(F.FpclbmError) as e:
+            lat.set_params(0.8, 0.7)  # order 3 rate 2.1
+        assert e.value.code == F.FPCLBM_ERR_PARAM
+        om = np.ones(27)
+        om[20] = 2.0
+        with pytest.raises(F.FpclbmError) as e:
+            lat.set_rates(om)
+        assert e.value.code == F.FPCLBM_ERR_PARAM
+        with pytest.raises(F.FpclbmError) as e:
+            lat.set_params(0.8, 0.0, F.FPCLBM_DIFF_FP_LEARNED)  # no closure installed
+        assert e.value.code == F.FPCLBM_ERR_STATE
+        with pytest.raises(F.FpclbmError):
+            lat.set_force(float("nan"), 0, 0)
+
+
+def test_graph_replay_equals_single_launches_bitwise():
+    n = 48
+    rho, ux, uy, uz = W.tgv(n, 0.05)
+    with make(n, n, n, "fp32", tau=0.55) as a, make(n, n, n, "fp32", tau=0.55) as b:
+        a.init_fields(rho, ux, uy, uz)
+        b.init_fields(rho, ux, uy, uz)
+        a.step(64)
+        for _ in range(64):
+            b.step(1)
+        for x, y in zip(a.moments(), b.moments()):
+            assert np.array_equal(x, y)
+
+
+def _sample_cells(nx, ny, nz, rng, k=12):
+    pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, nz // 2), (nx - 1, 0, 1), (nx // 2, ny // 2, nz // 2)]
+    pts += [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz))) for _ in range(k)]
+    return pts
+
+
+def _check_sampled(lat, shape_xyz, bc, Fv, om, unit, seed, steps=(1, 2)):
+    """Full-size run in the bench's launch configuration, checked at sampled cells against the oracle's
+    light-cone recursion started from the GPU's own stored initial populations."""
+    nx, ny, nz = shape_xyz
+    rng = np.random.default_rng(seed)
+    cells = _sample_cells(nx, ny, nz, rng)
+    # initial populations of every cell of the light cones (radius 2), read from the device
+    need = sorted({((x + dx) % nx, (y + dy) % ny, (z + dz) % nz) for x, y, z in cells
+                   for dx in range(-2, 3) for dy in range(-2, 3) for dz in range(-2, 3)})
+    flat = [x + nx * (y + ny * z) for x, y, z in need]
+    f0 = lat.populations_at(flat)
+    table = {c: f0[:, i] for i, c in enumerate(need)}
+    loc = LocalOracle((nz, ny, nx), lambda x, y, z: table[(x, y, z)], bc=bc, F=Fv, omega=om)
+    gmax = float(np.max(np.abs(f0 - W_REST[:, None])))  # largest stored deviation in the cones
+    flat_s = [x + nx * (y + ny * z) for x, y, z in cells]
+    t = 0
+    for target in steps:
+        lat.step(target - t)
+        t = target
+        got = lat.populations_at(flat_s)
+        for i, (x, y, z) in enumerate(cells):
+            ref = loc.pre(x, y, z, t)
+            # each step rounds the stored deviation once (<= unit |g|) and carries the earlier
+            # roundings through a collision of gain <~ 2: (2t - 1) unit (|g~| + max |g|)
+            bound = unit * (2 * t - 1) * (np.abs(ref - W_REST) + gmax) + 1e-6
+            assert np.all(np.abs(got[:, i] - ref) <= bound), (t, (x, y, z), np.max(np.abs(got[:, i] - ref)))
+
+
+def test_full_size_tgv_256_fp32_sampled():
+    """Config: TGV Re = 1600 at 256^3, FP32, sampled cells after one even and one odd step."""
+    n, u0 = 256, 0.05
+    nu = W.tgv_viscosity(n, u0, 1600.0)
+    tau = 3 * nu + 0.5
+    rho, ux, uy, uz = W.tgv(n, u0)
+    with make(n, n, n, "fp32", tau=tau) as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        _check_sampled(lat, (n, n, n), 0, (0, 0, 0), O.rates(tau), 0.0, seed=1)
+
+
+def test_full_size_channel_bf16_sampled():
+    """Config: channel 384 x 192 x 192, walls in y, body force, BF16 storage; sampled cells."""
+    nx, ny, nz = 384, 192, 192
+    u_star = 0.005
+    H = ny / 2
+    nu = u_star * H / 180.0
+    tau = 3 * nu + 0.5
+    Fx = u_star ** 2 / H
+    rho, ux, uy, uz = W.channel_fields(nx, ny, nz, u_star, seed=7)
+    with make(nx, ny, nz, "bf16", 1, (Fx, 0, 0), tau=tau) as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        _check_sampled(lat, (nx, ny, nz), 1, (Fx, 0, 0), O.rates(tau), 2.0 ** -8, seed=2)
+
+
+def test_fp32_velocity_error_after_1000_steps():
+    """Stated bound: FP32 path within 1e-5 (relative to u0) in velocity after 1000 steps of the
+    256^3 Re = 1600 TGV, against the FP64 GPU path (itself at oracle parity)."""
+    torch = pytest.importorskip("torch")
+    n, u0, steps = 256, 0.05, 1000
+    nu = W.tgv_viscosity(n, u0, 1600.0)
+    tau = 3 * nu + 0.5
+    rho, ux, uy, uz = W.tgv(n, u0)
+    outs = {}
+    for prec in ("fp64", "fp32"):
+        with make(n, n, n, prec, tau=tau) as lat:
+            lat.init_fields(rho, ux, uy, uz)
+            lat.step(steps)
+            dev = [torch.empty(n ** 3, dtype=torch.float64, device="cuda") for _ in range(4)]
+            F.fpclbm_moments(lat.h, *dev, on_device=1)
+            outs[prec] = dev
+    err = max(float((outs["fp32"][q] - outs["fp64"][q]).abs().max()) for q in (1, 2, 3)) / u0
+    print("fp32 max |du|/u0 after %d steps: %.3e" % (steps, err))
+    assert err <= 1e-5
