@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--inner", type=int, default=64, help="LBM steps per bench step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variants", action="store_true", help="also time fp16/bf16 storage")
+    p.add_argument("--workload", default="tgv", choices=["tgv", "channel", "ensemble"])
     return p.parse_args()
 
 
@@ -236,6 +237,39 @@ def time_ours(lat, F, torch, args, n, steps, warmup, inner):
     return e0.elapsed_time(e1) / 1e3
 
 
+def setup(args, F, prec, stream):
+    """Build the lattice of the chosen workload; returns (lat, flat fields, cells, config dict)."""
+    if args.workload == "tgv":
+        n, u0 = args.n, 0.05
+        tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
+        lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_PERIODIC, stream=stream)
+        lat.set_params(tau)
+        flds = W.tgv(n, u0)
+        cfg = {"workload": "TGV Re=1600 %d^3 periodic, u0=0.05, tau=%.6f" % (n, tau)}
+    elif args.workload == "channel":
+        nx, ny, nz, u_star = 384, 192, 192, 0.005
+        H = ny / 2
+        tau = 3 * (u_star * H / 180.0) + 0.5
+        lat = F.Lattice(nx, ny, nz, prec, F.FPCLBM_BC_WALLS_Y, stream=stream)
+        lat.set_params(tau)
+        lat.set_force(u_star ** 2 / H, 0.0, 0.0)
+        flds = W.channel_fields(nx, ny, nz, u_star, seed=7)
+        cfg = {"workload": "channel Re_tau=180 384x192x192, y walls, body force, tau=%.6f" % tau}
+    else:
+        sides, taus = W.ensemble_config(256, seed=2410)
+        dims = [(s_, s_, s_) for s_ in sides]
+        lat = F.Lattice.ensemble(dims, taus, "fp32", stream=stream)
+        lat.set_params(1.0)
+        flds = W.ensemble_fields(sides, seed=2410)
+        cfg = {"workload": "ensemble of 256 periodic boxes, sides in {32,48,64,96}, tau in [0.505,0.6], "
+                           "solenoidal u_rms=0.04", "cells": int(sum(s_ ** 3 for s_ in sides))}
+    flat = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1) for a in flds]
+    if len(flat[0]) != lat.ncells:
+        flat = [np.concatenate([np.asarray(f[q]).reshape(-1) for f in flds]) for q in range(4)]
+    lat.init_fields(*flat)
+    return lat, flat, lat.ncells, cfg
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -245,31 +279,29 @@ def main():
     import torch
     from paper_2410_09739_gb300 import fpclbm as F
     torch.cuda.set_device(local)
-    n, u0 = args.n, 0.05
-    nu = W.tgv_viscosity(n, u0, 1600.0)
-    tau = 3 * nu + 0.5
-    rho, ux, uy, uz = W.tgv(n, u0)
-    ncell = n ** 3
     stream = torch.cuda.current_stream().cuda_stream
+    prec0 = args.precision if args.workload != "ensemble" else "fp32"
     results = {}
-    precs = [args.precision] + ([p for p in ("fp16", "bf16") if p != args.precision] if args.variants else [])
+    precs = [prec0] + ([p for p in ("fp16", "bf16") if p != prec0] if args.variants and args.workload != "ensemble"
+                       else [])
+    cfg = None
     for prec in precs:
-        lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_PERIODIC, stream=stream)
-        lat.set_params(tau)
-        lat.init_fields(rho, ux, uy, uz)
+        lat, flat, ncell, c = setup(args, F, prec, stream)
+        if cfg is None:
+            cfg = c
         barrier(world)
-        clocks = Clocks(local) if (rank == 0 and prec == args.precision) else None
+        clocks = Clocks(local) if (rank == 0 and prec == prec0) else None
         if clocks:
             clocks.start()
-        el = time_ours(lat, F, torch, args, n, args.steps, args.warmup, args.inner)
+        el = time_ours(lat, F, torch, args, ncell, args.steps, args.warmup, args.inner)
         ck = clocks.stop() if clocks else None
         el = max_over_ranks(el, world)
         results[prec] = {"seconds": el, "clocks": ck}
-        if prec == args.precision:
+        if prec == prec0:
             # e2e: host buffers through the C ABI, copies inside the timed region
             hb = [torch.empty(ncell, dtype=torch.float64).pin_memory().numpy() for _ in range(8)]
-            for a, src in zip(hb[:4], (rho, ux, uy, uz)):
-                a[:] = np.asarray(src).reshape(-1)
+            for a, src in zip(hb[:4], flat):
+                a[:] = src
             for _ in range(2):
                 F.fpclbm_init_fields(lat.h, *hb[:4], on_device=0)
                 lat.step(args.inner)
@@ -280,32 +312,31 @@ def main():
                 F.fpclbm_init_fields(lat.h, *hb[:4], on_device=0)
                 lat.step(args.inner)
                 F.fpclbm_moments(lat.h, *hb[4:], on_device=0)
-            e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-            results[prec]["e2e_s"] = e2e_s
+            results[prec]["e2e_s"] = max_over_ranks(time.perf_counter() - t0, world)
         lat.close()
     if rank != 0:
         return
-    prec = args.precision
+    prec = prec0
     el = results[prec]["seconds"]
-    lups = ncell * args.inner * args.steps * world
-    value = lups / el / 1e6
+    value = ncell * args.inner * args.steps * world / el / 1e6
     launches = args.inner * args.steps
     per_launch = el / launches
     alg_bytes = 54 * BYTES[prec] * ncell
     peak, peak_kind = peaks()
     achieved = alg_bytes / per_launch / 1e9
+    cfg.update({"precision": prec, "storage": prec, "lbm_steps_per_bench_step": args.inner,
+                "l2": "inputs larger than L2 (%.2f GB populations)" % (27 * BYTES[prec] * ncell / 1e9),
+                "parallelism": "replicas" if world > 1 else "1 GPU"})
+    kname = "fpc::k_ens_step (persistent, AA even/odd)" if args.workload == "ensemble" else "fpc::k_step (AA even/odd)"
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
-        "config": {"workload": "TGV Re=1600 %d^3 periodic, u0=0.05, tau=%.6f" % (n, tau), "precision": prec,
-                   "storage": prec, "lbm_steps_per_bench_step": args.inner,
-                   "l2": "inputs larger than L2 (%.2f GB populations)" % (27 * BYTES[prec] * ncell / 1e9),
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(prec, n),
-                     "peak_source": peak_kind, "kernel": "fpc::k_step (AA even/odd)",
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "frac": achieved / peak,
+                     "traffic": ncu_traffic(prec, args.n) if args.workload == "tgv" else None,
+                     "peak_source": peak_kind, "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": ncell * args.inner * args.steps * world / results[prec]["e2e_s"] / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": 4 * 8 * ncell, "d2h_bytes_per_step": 4 * 8 * ncell},
         "gpu_launches": launches,
@@ -316,7 +347,8 @@ def main():
                                "frac_hbm": 54 * BYTES[p] * ncell / (r["seconds"] / launches) / 1e9 / peak}
                            for p, r in results.items()}
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_oracle_sample(n, tau, u0)
+        n, u0 = args.n, 0.05
+        out["cpu_baseline"] = cpu_oracle_sample(n, 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5, u0)
     print(json.dumps(out), flush=True)
 
 

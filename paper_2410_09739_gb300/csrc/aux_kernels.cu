@@ -284,14 +284,17 @@ cudaError_t launch_set_pops(int precision, const BoxGeom& b, const double* in, u
     return cudaGetLastError();
 }
 
-cudaError_t launch_diagnostics(int precision, const BoxGeom& b, int parity, double Fx, double Fy, double Fz,
-                               double* part, double* out, cudaStream_t st)
+cudaError_t launch_diag_partial(int precision, const BoxGeom& b, int parity, double Fx, double Fy, double Fz,
+                                double* part, cudaStream_t st)
 {
     const int nb = diag_blocks(b.ncells);
     FPC_DISPATCH(precision, (k_diag_partial<S><<<nb, kDiagThreads, 0, st>>>(b, parity, Fx, Fy, Fz, part)));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_diag_final<<<1, kDiagThreads, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_final(const double* part, int nparts, double* out, cudaStream_t st)
+{
+    k_diag_final<<<1, kDiagThreads, 0, st>>>(part, nparts, out);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,60 @@ struct CellGeom {
     FastDiv div_nx, div_nxny;
 };
 
+// Neighbour coordinates of a cell for the odd step: column, row offset and
+// plane offset of x - e for e = -1, 0, +1 (index 0, 1, 2), and whether the
+// source row lies inside the fluid (y walls).
+struct Nbr {
+    unsigned xs[3], yr[3], zp[3];
+    bool yin[3];
+};
+
+template <bool WALLS>
+__device__ __forceinline__ Nbr make_nbr(const CellGeom& G, unsigned cell)
+{
+    Nbr n;
+    const unsigned nx = G.nx, ny = G.ny, nz = G.nz, nxny = nx * ny;
+    const unsigned z = fdiv(cell, G.div_nxny);
+    const unsigned rem = cell - z * nxny;
+    const unsigned y = fdiv(rem, G.div_nx);
+    const unsigned x = rem - y * nx;
+    n.xs[0] = (x + 1 == nx) ? 0u : x + 1;
+    n.xs[1] = x;
+    n.xs[2] = (x == 0) ? nx - 1 : x - 1;
+    const unsigned yp = (y + 1 == ny) ? 0u : y + 1, ym = (y == 0) ? ny - 1 : y - 1;
+    n.yr[0] = yp * nx;
+    n.yr[1] = y * nx;
+    n.yr[2] = ym * nx;
+    n.yin[0] = WALLS ? (y + 1 < ny) : true;
+    n.yin[1] = true;
+    n.yin[2] = WALLS ? (y > 0) : true;
+    const unsigned zpp = (z + 1 == nz) ? 0u : z + 1, zmm = (z == 0) ? nz - 1 : z - 1;
+    n.zp[0] = zpp * nxny;
+    n.zp[1] = z * nxny;
+    n.zp[2] = zmm * nxny;
+    return n;
+}
+
+// Element offset read for slot s (the population that streams into the cell).
+template <bool ODD, bool WALLS>
+__device__ __forceinline__ unsigned load_off(int s, const Nbr& n, unsigned stride, unsigned cell)
+{
+    if (!ODD) return s * stride + cell;
+    const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
+    if (WALLS && !n.yin[iy]) return s * stride + cell;
+    return (26 - s) * stride + n.xs[ix] + n.yr[iy] + n.zp[iz];
+}
+
+// Element offset written for slot s (the destination of the post-collision value).
+template <bool ODD, bool WALLS>
+__device__ __forceinline__ unsigned store_off(int s, const Nbr& n, unsigned stride, unsigned cell)
+{
+    if (!ODD) return (26 - s) * stride + cell;
+    const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
+    if (WALLS && !n.yin[2 - iy]) return (26 - s) * stride + cell;
+    return s * stride + n.xs[2 - ix] + n.yr[2 - iy] + n.zp[2 - iz];
+}
+
 template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE>
 __device__ __forceinline__ void update_cell(S* __restrict__ buf, const CellGeom& G, unsigned cell,
                                             const Rates<R>& rt, R Fx, R Fy, R Fz, R om4, R om5, R om6, R om8,
@@ -33,59 +87,16 @@ __device__ __forceinline__ void update_cell(S* __restrict__ buf, const CellGeom&
 {
     const unsigned stride = G.stride;
     R g[27];
-    unsigned xs[3], yr[3], zp[3];  // source column, row offset, plane offset for e = -1, 0, +1
-    bool yin[3];                   // source row inside the fluid (walls)
-    if (ODD) {
-        const unsigned nx = G.nx, ny = G.ny, nz = G.nz, nxny = nx * ny;
-        const unsigned z = fdiv(cell, G.div_nxny);
-        const unsigned rem = cell - z * nxny;
-        const unsigned y = fdiv(rem, G.div_nx);
-        const unsigned x = rem - y * nx;
-        // source of slot component e is x - e
-        xs[0] = (x + 1 == nx) ? 0u : x + 1;
-        xs[1] = x;
-        xs[2] = (x == 0) ? nx - 1 : x - 1;
-        const unsigned yp = (y + 1 == ny) ? 0u : y + 1, ym = (y == 0) ? ny - 1 : y - 1;
-        yr[0] = yp * nx;
-        yr[1] = y * nx;
-        yr[2] = ym * nx;
-        yin[0] = WALLS ? (y + 1 < ny) : true;
-        yin[1] = true;
-        yin[2] = WALLS ? (y > 0) : true;
-        const unsigned zpp = (z + 1 == nz) ? 0u : z + 1, zmm = (z == 0) ? nz - 1 : z - 1;
-        zp[0] = zpp * nxny;
-        zp[1] = z * nxny;
-        zp[2] = zmm * nxny;
+    Nbr n;
+    if (ODD) n = make_nbr<WALLS>(G, cell);
 #pragma unroll
-        for (int s = 0; s < 27; ++s) {
-            const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
-            if (WALLS && !yin[iy])
-                g[s] = Store<S>::ld(buf + (size_t)(s * stride + cell));
-            else
-                g[s] = Store<S>::ld(buf + (size_t)((26 - s) * stride + xs[ix] + yr[iy] + zp[iz]));
-        }
-    } else {
-#pragma unroll
-        for (int s = 0; s < 27; ++s) g[s] = Store<S>::ld(buf + (size_t)(s * stride + cell));
-    }
+    for (int s = 0; s < 27; ++s) g[s] = Store<S>::ld(buf + (size_t)load_off<ODD, WALLS>(s, n, stride, cell));
 
     const bool ok = collide_cell<R, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, closure);
     if (!ok) atomicOr(flag, 1);
 
-    if (ODD) {
-        // destination of slot component e is x + e: the source of -e
 #pragma unroll
-        for (int s = 0; s < 27; ++s) {
-            const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
-            if (WALLS && !yin[2 - iy])
-                Store<S>::st(buf + (size_t)((26 - s) * stride + cell), g[s]);
-            else
-                Store<S>::st(buf + (size_t)(s * stride + xs[2 - ix] + yr[2 - iy] + zp[2 - iz]), g[s]);
-        }
-    } else {
-#pragma unroll
-        for (int s = 0; s < 27; ++s) Store<S>::st(buf + (size_t)((26 - s) * stride + cell), g[s]);
-    }
+    for (int s = 0; s < 27; ++s) Store<S>::st(buf + (size_t)store_off<ODD, WALLS>(s, n, stride, cell), g[s]);
 }
 
 }  // namespace fpc

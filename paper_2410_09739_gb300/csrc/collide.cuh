@@ -176,14 +176,16 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
         om9 = fmin(fmax(om9 + dw, lo), hi);
     }
 
-    // order 1 (attractor 0, source F)
-    FPC_D(1, 0, 0) = rt.keep[1] * FPC_D(1, 0, 0);
-    FPC_D(0, 1, 0) = rt.keep[2] * FPC_D(0, 1, 0);
-    FPC_D(0, 0, 1) = rt.keep[3] * FPC_D(0, 0, 1);
+    // order 1 (attractor 0, source F).  In exact arithmetic kappa_100 = -F_x/2 and
+    // kappa~_100 = F_x/2 whatever omega_1..3 are, so they are applied here as 0:
+    // kappa~_100 = kappa_100 + F_x keeps the rounding residual j - rho u of the forward
+    // transform, and the back transform then rebuilds the momentum j + F to the last
+    // bit instead of rho * round(j / rho) (whose error repeats every step in a slowly
+    // varying flow and would accumulate linearly in fp32).
     if (FORCE) {
-        FPC_D(1, 0, 0) = fmaR(rt.src[1], Fx, FPC_D(1, 0, 0));
-        FPC_D(0, 1, 0) = fmaR(rt.src[2], Fy, FPC_D(0, 1, 0));
-        FPC_D(0, 0, 1) = fmaR(rt.src[3], Fz, FPC_D(0, 0, 1));
+        FPC_D(1, 0, 0) += Fx;
+        FPC_D(0, 1, 0) += Fy;
+        FPC_D(0, 0, 1) += Fz;
     }
 
     // sources of order 3 from the pre-collision second moments

@@ -43,7 +43,9 @@ __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f)
 }
 
 // Relaxation data of one box: omega_j, 1 - omega_j, 1 - omega_j / 2 in the
-// numbering of Appendix D Step 3 (0:000 ... 26:222).
+// numbering of Appendix D Step 3 (0:000 ... 26:222).  Entries 0..3 (the
+// conserved moments) are not read by the kernels: they cancel in exact
+// arithmetic (see collide.cuh, order 1).
 template <typename R>
 struct Rates {
     R om[27];

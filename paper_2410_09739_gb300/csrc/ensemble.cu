@@ -1,8 +1,213 @@
-// ensemble.cu -- placeholder, replaced by the ensemble implementation.
-#include "../../include/fpclbm.h"
-#include "internal.h"
-extern "C" int fpclbm_create_ensemble(fpclbm_t* out, int, const int*, const double*, int, void*)
+// ensemble.cu -- many independent periodic boxes of uneven sizes and
+// viscosities advanced by ONE persistent launch per time step.
+//
+// Every box keeps its own SoA population block (27 slot rows of stride_b
+// elements, AA pattern, see cell.cuh).  The cells of all boxes are cut into
+// tiles of `block` cells (a box's last tile is ragged); tile t belongs to box
+// tile_box[t].  A persistent grid of SMs x resident-blocks strides over the
+// tile list; each tile runs the same per-cell update as a single box, with
+// the box's own geometry and shear rate 1/tau_b.  Boxes never exchange data.
+#include <cstring>
+#include <vector>
+
+#include "cell.cuh"
+#include "handle.h"
+
+namespace fpc {
+
+template <bool ODD, bool FORCE, int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ens_step(const EnsArgs a)
 {
-    if (out) *out = nullptr;
-    return FPCLBM_ERR_ARG;
+    float* __restrict__ base = static_cast<float*>(a.buf);
+    for (unsigned t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const unsigned b = __ldg(a.tile_box + t);
+        const EnsBox& B = a.boxes[b];
+        const unsigned first = (t - __ldg(&B.tile0)) * a.tile_cells;
+        const unsigned ncells = __ldg(&B.ncells);
+        CellGeom G;
+        G.stride = __ldg(&B.stride);
+        G.nx = __ldg(&B.nx);
+        G.ny = __ldg(&B.ny);
+        G.nz = __ldg(&B.nz);
+        G.div_nx.d = __ldg(&B.div_nx.d);
+        G.div_nx.m = __ldg(&B.div_nx.m);
+        G.div_nx.s = __ldg(&B.div_nx.s);
+        G.div_nxny.d = __ldg(&B.div_nxny.d);
+        G.div_nxny.m = __ldg(&B.div_nxny.m);
+        G.div_nxny.s = __ldg(&B.div_nxny.s);
+        const float om = __ldg(&B.om_shear);
+        float* buf = base + __ldg(&B.off);
+        for (unsigned c = threadIdx.x; c < a.tile_cells; c += blockDim.x) {
+            const unsigned cell = first + c;
+            if (cell >= ncells) break;
+            update_cell<float, float, ODD, false, FORCE, MODE>(buf, G, cell, a.rates, a.Fx, a.Fy, a.Fz, om, om, om, om,
+                                                               om, nullptr, a.flag);
+        }
+    }
+}
+
+template <bool ODD, bool FORCE, int MODE>
+static cudaError_t go(const EnsArgs& a, int block, int minb, int grid, cudaStream_t st)
+{
+    if (minb == 3)
+        k_ens_step<ODD, FORCE, MODE, 3><<<grid, block, 0, st>>>(a);
+    else
+        k_ens_step<ODD, FORCE, MODE, 2><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ens_step(int odd, int force, int mode, const EnsArgs& a, int block, int minb, int grid,
+                            cudaStream_t st)
+{
+    if (grid <= 0 || block <= 0 || block > 256 || a.tile_cells % block != 0) return cudaErrorInvalidValue;
+#define FPC_ENS(O, Fo, M) return go<O, Fo, M>(a, block, minb, grid, st)
+    if (mode == MODE_FP) {
+        if (odd) { if (force) FPC_ENS(true, true, MODE_FP); FPC_ENS(true, false, MODE_FP); }
+        if (force) FPC_ENS(false, true, MODE_FP);
+        FPC_ENS(false, false, MODE_FP);
+    }
+    if (mode == MODE_EQ) {
+        if (odd) { if (force) FPC_ENS(true, true, MODE_EQ); FPC_ENS(true, false, MODE_EQ); }
+        if (force) FPC_ENS(false, true, MODE_EQ);
+        FPC_ENS(false, false, MODE_EQ);
+    }
+#undef FPC_ENS
+    return cudaErrorInvalidValue;
+}
+
+int ens_max_blocks_per_sm(int block, int minb, int mode)
+{
+    int n = 0;
+    cudaError_t e;
+    if (mode == MODE_EQ)
+        e = minb == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_EQ, 3>, block, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_EQ, 2>, block, 0);
+    else
+        e = minb == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_FP, 3>, block, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_FP, 2>, block, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+}  // namespace fpc
+
+using namespace fpc;
+
+extern "C" int fpclbm_create_ensemble(fpclbm_t* out, int n_boxes, const int* dims, const double* tau, int precision,
+                                      void* cuda_stream)
+{
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return FPCLBM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (n_boxes < 1 || !dims || !tau) {
+        g_create_error = "need n_boxes >= 1, dims and tau";
+        return FPCLBM_ERR_ARG;
+    }
+    if (precision != FPCLBM_FP32) {
+        g_create_error = "ensembles support FPCLBM_FP32 only";
+        return FPCLBM_ERR_ARG;
+    }
+    fpclbm* h = new (std::nothrow) fpclbm();
+    if (!h) {
+        g_create_error = "host allocation failed";
+        return FPCLBM_ERR_ALLOC;
+    }
+    h->ensemble = true;
+    h->precision = precision;
+    h->bc = FPCLBM_BC_PERIODIC;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    rates_from_params(1.0, 0.0, h->omega);
+    unsigned long long off = 0, cells = 0;
+    const int tile = 256;  // cells per tile = the largest block size the tuner may pick
+    unsigned tiles = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+        const int nx = dims[3 * b], ny = dims[3 * b + 1], nz = dims[3 * b + 2];
+        if (nx < 1 || ny < 1 || nz < 1) {
+            g_create_error = "box dimensions must be >= 1";
+            delete h;
+            return FPCLBM_ERR_ARG;
+        }
+        const double w = 1.0 / tau[b];
+        if (!(w > 0.0 && w < 2.0)) {
+            g_create_error = "box " + std::to_string(b) + ": 1/tau outside (0, 2)";
+            delete h;
+            return FPCLBM_ERR_PARAM;
+        }
+        Box bx;
+        bx.nx = nx;
+        bx.ny = ny;
+        bx.nz = nz;
+        const unsigned long long n = (unsigned long long)nx * ny * nz;
+        bx.ncells = (unsigned)n;
+        bx.stride = (unsigned)((n + 63) / 64 * 64);
+        bx.off = off;
+        bx.cell0 = (unsigned)cells;
+        bx.tau = tau[b];
+        bx.tile0 = tiles;
+        bx.ntiles = (unsigned)((n + tile - 1) / tile);
+        off += 27ull * bx.stride;
+        cells += n;
+        tiles += bx.ntiles;
+        if (n >= (1ull << 31) || 27ull * bx.stride >= (1ull << 32) || cells >= (1ull << 32)) {
+            g_create_error = "ensemble too large";
+            delete h;
+            return FPCLBM_ERR_ARG;
+        }
+        h->boxes.push_back(bx);
+    }
+    h->total_cells = cells;
+    h->ntiles = tiles;
+    h->tile_cells = tile;
+    int rc = alloc_common(h);
+    cudaError_t e = cudaSuccess;
+    if (rc == FPCLBM_OK) {
+        e = cudaMalloc(&h->d_pop, off * elem_size(precision));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_ens_boxes, sizeof(EnsBox) * n_boxes);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_tile_box, sizeof(unsigned) * tiles);
+        if (e == cudaSuccess) {
+            std::vector<EnsBox> tab(n_boxes);
+            std::vector<unsigned> tb(tiles);
+            for (int b = 0; b < n_boxes; ++b) {
+                const Box& bx = h->boxes[b];
+                EnsBox& E = tab[b];
+                std::memset(&E, 0, sizeof E);
+                E.off = bx.off;
+                E.stride = bx.stride;
+                E.ncells = bx.ncells;
+                E.nx = bx.nx;
+                E.ny = bx.ny;
+                E.nz = bx.nz;
+                E.div_nx = make_fastdiv((unsigned)bx.nx);
+                E.div_nxny = make_fastdiv((unsigned)(bx.nx * bx.ny));
+                E.om_shear = (float)(1.0 / bx.tau);
+                E.tile0 = bx.tile0;
+                for (unsigned t = 0; t < bx.ntiles; ++t) tb[bx.tile0 + t] = (unsigned)b;
+            }
+            e = cudaMemcpyAsync(h->d_ens_boxes, tab.data(), sizeof(EnsBox) * n_boxes, cudaMemcpyHostToDevice,
+                                h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->d_tile_box, tb.data(), sizeof(unsigned) * tiles, cudaMemcpyHostToDevice,
+                                    h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        }
+        if (e != cudaSuccess) {
+            g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
+            rc = e == cudaErrorMemoryAllocation ? FPCLBM_ERR_ALLOC : FPCLBM_ERR_CUDA;
+        }
+    }
+    if (rc != FPCLBM_OK) {
+        fpclbm_destroy(h);
+        return rc;
+    }
+    h->block = tile;
+    h->minb = 2;
+    h->grid = h->sm_count * ens_max_blocks_per_sm(tile, 2, MODE_FP);
+    *out = h;
+    return FPCLBM_OK;
 }

@@ -1,63 +1,28 @@
 // fpclbm.cu -- host runtime and C ABI of libfpclbm.so (see include/fpclbm.h).
 //
-// A handle owns one population buffer (AA pattern, one copy), a divergence
-// flag, staging buffers for host transfers, and a cached CUDA graph of the
-// step loop.  Relaxation rates (Appendix D Step 3 numbering) and the body
-// force live in the handle and are passed to every launch by value.
+// A handle owns one population buffer (AA pattern, one copy per box), a
+// divergence flag, staging buffers for host transfers, and a cached CUDA
+// graph of the step loop.  Relaxation rates (Appendix D Step 3 numbering) and
+// the body force live in the handle and are passed to every launch by value.
+// On the first fpclbm_step of a large enough handle the launch configuration
+// is autotuned on a saved copy of the state (the state is restored bit for
+// bit afterwards), and the choice is cached per device and configuration.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
-#include "../../include/fpclbm.h"
-#include "internal.h"
+#include "handle.h"
 
 using namespace fpc;
 
-namespace {
+namespace fpc {
 
 thread_local std::string g_create_error;
-
-constexpr int kGraphSteps = 32;           // steps per captured graph (even)
-constexpr unsigned kChunk = 1u << 20;     // cells per host-transfer chunk
-
-}  // namespace
-
-struct fpclbm {
-    // geometry
-    int nx = 0, ny = 0, nz = 0;
-    unsigned ncells = 0, stride = 0;
-    int precision = 0, bc = 0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    int device = 0;
-    // state
-    void* d_pop = nullptr;
-    int* d_flag = nullptr;
-    int* h_flag = nullptr;  // pinned
-    double* d_stage = nullptr;
-    size_t stage_bytes = 0;
-    double* d_part = nullptr;
-    double* d_diag = nullptr;
-    double* h_diag = nullptr;  // pinned
-    float* d_closure = nullptr;
-    bool have_closure = false;
-    bool initialized = false;
-    long long steps = 0;
-    // parameters
-    double omega[27];
-    double F[3] = {0, 0, 0};
-    int diffusion = FPCLBM_DIFF_FP;
-    // launch config and graph cache
-    StepLaunch launch{256};
-    cudaGraphExec_t graph = nullptr;
-    bool graph_valid = false;
-    std::string err;
-};
-
-namespace {
 
 int fail(fpclbm* h, int code, const std::string& msg)
 {
@@ -70,14 +35,9 @@ int cuda_fail(fpclbm* h, cudaError_t e, const char* what)
     return fail(h, FPCLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define FPC_CK(h, call, what)                          \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
-    } while (0)
-
-// Rates from (tau, drift): shear 1/tau on 4,5,6,8,9; bulk 1 on 7; 1 on 0..3;
-// orders >= 3: k * drift, or 1 when drift == 0.
+// Rates from (tau, drift): shear 1/tau on 4,5,6,8,9 (Eq. transportcoeff3DFPCLBM);
+// bulk 1 on 7 and 1 on 0..3; orders >= 3: k * drift (omega_mnp = (m+n+p) omega_FP),
+// or 1 when drift == 0 (unit higher-order rates, Sec. 4).
 void rates_from_params(double tau, double drift, double om[27])
 {
     static const int order[27] = {0, 1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 5, 5, 5, 6};
@@ -107,18 +67,71 @@ bool rates_valid(const double om[27], std::string& why)
     return true;
 }
 
+size_t elem_size(int precision)
+{
+    switch (precision) {
+        case FPCLBM_FP64: return 8;
+        case FPCLBM_FP32: return 4;
+        default: return 2;
+    }
+}
+
+int alloc_common(fpclbm* h)
+{
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_flag, sizeof(int));
+    unsigned parts = 0;
+    for (auto& b : h->boxes) {
+        b.diag0 = parts;
+        parts += (unsigned)diag_blocks(b.ncells);
+    }
+    h->diag_parts = parts;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_part, sizeof(double) * 5 * (size_t)parts);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, sizeof(double) * 5);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_diag, sizeof(double) * 5);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? FPCLBM_ERR_ALLOC : FPCLBM_ERR_CUDA;
+    }
+    return FPCLBM_OK;
+}
+
+}  // namespace fpc
+
+namespace {
+
+constexpr int kGraphSteps = 32;        // steps per captured graph (even)
+constexpr unsigned kChunk = 1u << 20;  // cells per host-transfer chunk
+
+#define FPC_CK(h, call, what)                                 \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+void* box_ptr(const fpclbm* h, const Box& b)
+{
+    return static_cast<char*>(h->d_pop) + b.off * elem_size(h->precision);
+}
+
 template <typename R>
 StepArgs<R> make_args(const fpclbm* h)
 {
+    const Box& b = h->boxes[0];
     StepArgs<R> a;
-    a.buf = h->d_pop;
-    a.stride = h->stride;
-    a.ncells = h->ncells;
-    a.nx = h->nx;
-    a.ny = h->ny;
-    a.nz = h->nz;
-    a.div_nx = make_fastdiv((unsigned)h->nx);
-    a.div_nxny = make_fastdiv((unsigned)(h->nx * h->ny));
+    a.buf = box_ptr(h, b);
+    a.stride = b.stride;
+    a.ncells = b.ncells;
+    a.nx = b.nx;
+    a.ny = b.ny;
+    a.nz = b.nz;
+    a.div_nx = make_fastdiv((unsigned)b.nx);
+    a.div_nxny = make_fastdiv((unsigned)(b.nx * b.ny));
     a.Fx = (R)h->F[0];
     a.Fy = (R)h->F[1];
     a.Fz = (R)h->F[2];
@@ -132,19 +145,39 @@ StepArgs<R> make_args(const fpclbm* h)
     return a;
 }
 
-BoxGeom geom_of(const fpclbm* h)
+EnsArgs make_ens_args(const fpclbm* h)
 {
-    BoxGeom b;
-    b.buf = h->d_pop;
-    b.stride = h->stride;
-    b.ncells = h->ncells;
-    b.nx = h->nx;
-    b.ny = h->ny;
-    b.nz = h->nz;
-    b.walls = h->bc == FPCLBM_BC_WALLS_Y;
-    b.div_nx = make_fastdiv((unsigned)h->nx);
-    b.div_nxny = make_fastdiv((unsigned)(h->nx * h->ny));
-    return b;
+    EnsArgs a;
+    a.buf = h->d_pop;
+    a.boxes = h->d_ens_boxes;
+    a.tile_box = h->d_tile_box;
+    a.ntiles = h->ntiles;
+    a.tile_cells = (unsigned)h->tile_cells;
+    for (int j = 0; j < 27; ++j) {
+        a.rates.om[j] = (float)h->omega[j];
+        a.rates.keep[j] = (float)(1.0 - h->omega[j]);
+        a.rates.src[j] = (float)(1.0 - 0.5 * h->omega[j]);
+    }
+    a.Fx = (float)h->F[0];
+    a.Fy = (float)h->F[1];
+    a.Fz = (float)h->F[2];
+    a.flag = h->d_flag;
+    return a;
+}
+
+BoxGeom geom_of(const fpclbm* h, const Box& b)
+{
+    BoxGeom g;
+    g.buf = box_ptr(h, b);
+    g.stride = b.stride;
+    g.ncells = b.ncells;
+    g.nx = b.nx;
+    g.ny = b.ny;
+    g.nz = b.nz;
+    g.walls = h->bc == FPCLBM_BC_WALLS_Y;
+    g.div_nx = make_fastdiv((unsigned)b.nx);
+    g.div_nxny = make_fastdiv((unsigned)(b.nx * b.ny));
+    return g;
 }
 
 int mode_of(const fpclbm* h)
@@ -156,12 +189,15 @@ int mode_of(const fpclbm* h)
 
 bool has_force(const fpclbm* h) { return h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0; }
 
-cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st)
+cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st, int block, int minb, int grid, int pipe)
 {
+    if (h->ensemble)
+        return launch_ens_step((int)(t & 1), has_force(h), mode_of(h), make_ens_args(h), block, minb, grid, st);
     const StepArgs<double> a64 = make_args<double>(h);
     const StepArgs<float> a32 = make_args<float>(h);
-    return launch_step(h->precision, (int)(t & 1), h->bc == FPCLBM_BC_WALLS_Y, has_force(h), mode_of(h), a64, a32,
-                       h->launch, st);
+    StepLaunch cfg{block, minb, pipe};
+    return launch_step(h->precision, (int)(t & 1), h->bc == FPCLBM_BC_WALLS_Y, has_force(h), mode_of(h), a64, a32, cfg,
+                       st);
 }
 
 void drop_graph(fpclbm* h)
@@ -177,7 +213,7 @@ int build_graph(fpclbm* h)
     cudaGraph_t g = nullptr;
     FPC_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = one_step(h, k, h->cap_stream);
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = one_step(h, k, h->cap_stream, h->block, h->minb, h->grid, h->pipe);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -203,13 +239,120 @@ int ensure_stage(fpclbm* h, size_t bytes)
     return FPCLBM_OK;
 }
 
-size_t elem_size(int precision)
+unsigned chunk_of(const Box& b) { return b.ncells < kChunk ? b.ncells : kChunk; }
+
+// ---------------------------------------------------------------------------
+// Autotuning of the launch configuration (block size; persistent grid for
+// ensembles).  Runs on the handle's own buffer after saving it to a device
+// copy, times every candidate from the same state, restores the state, and
+// caches the winner per device/precision/boundary/force/mode/shape class.
+// ---------------------------------------------------------------------------
+
+struct TuneChoice {
+    int block, minb, grid, pipe;
+};
+
+bool verbose()
 {
-    switch (precision) {
-        case FPCLBM_FP64: return 8;
-        case FPCLBM_FP32: return 4;
-        default: return 2;
+    const char* v = std::getenv("FPCLBM_VERBOSE");
+    return v && v[0] && v[0] != '0';
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+
+std::string tune_key(const fpclbm* h)
+{
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "dev%d/p%d/bc%d/f%d/m%d/%s/%llu", h->device, h->precision, h->bc, (int)has_force(h),
+                  mode_of(h), h->ensemble ? "ens" : "box", (unsigned long long)(h->total_cells >> 20));
+    return buf;
+}
+
+int autotune(fpclbm* h)
+{
+    h->tuned = true;
+    std::vector<TuneChoice> cands;
+    const bool fp32_math = h->precision != FPCLBM_FP64 && mode_of(h) != MODE_LEARNED;
+    const bool pipe_ok = elem_size(h->precision) >= 4;  // cp.async moves >= 4 bytes
+    if (h->ensemble) {
+        for (int minb : {2, 3})
+            for (int block : {128, 256}) {
+                const int per_sm = ens_max_blocks_per_sm(block, minb, mode_of(h));
+                for (int mult : {1, 2}) cands.push_back({block, minb, h->sm_count * per_sm * mult, 0});
+            }
+    } else if (fp32_math) {
+        for (int minb : {2, 3, 4})
+            for (int block : {128, 256}) cands.push_back({block, minb, 0, 0});
+        if (pipe_ok)
+            for (int minb : {2, 3, 4}) cands.push_back({128, minb, 0, 1});
+    } else {
+        for (int block : {128, 256}) cands.push_back({block, 1, 0, 0});
+        if (pipe_ok && mode_of(h) != MODE_LEARNED) cands.push_back({128, 1, 0, 1});
     }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(h));
+        if (it != g_tune_cache.end()) {
+            h->block = it->second.block;
+            h->minb = it->second.minb;
+            h->grid = it->second.grid;
+            h->pipe = it->second.pipe;
+            return FPCLBM_OK;
+        }
+    }
+    h->block = cands[0].block;
+    h->minb = cands[0].minb;
+    h->grid = cands[0].grid;
+    h->pipe = cands[0].pipe;
+    // small problems: keep the first candidate, tuning noise would dominate
+    if (h->total_cells < (1ull << 20)) return FPCLBM_OK;
+    size_t bytes = 0;
+    for (const Box& b : h->boxes) bytes += 27ull * b.stride * elem_size(h->precision);
+    void* backup = nullptr;
+    if (cudaMalloc(&backup, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FPCLBM_OK;  // no room to tune safely: keep the default
+    }
+    FPC_CK(h, cudaMemcpyAsync(backup, h->d_pop, bytes, cudaMemcpyDeviceToDevice, h->stream), "tune save");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    TuneChoice win = cands[0];
+    for (const TuneChoice& c : cands) {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = one_step(h, h->steps + k, h->stream, c.block, c.minb, c.grid, c.pipe);
+        cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = one_step(h, h->steps + k, h->stream, c.block, c.minb, c.grid, c.pipe);
+        cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (verbose())
+            std::fprintf(stderr, "fpclbm tune %s: block %d minb %d grid %d pipe %d: %.4f ms/step%s\n",
+                         tune_key(h).c_str(), c.block, c.minb, c.grid, c.pipe, ms / 8,
+                         e == cudaSuccess ? "" : " (launch failed)");
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            win = c;
+        }
+        if (e != cudaSuccess) cudaGetLastError();
+        cudaMemcpyAsync(h->d_pop, backup, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(backup);
+    FPC_CK(h, e, "tune restore");
+    h->block = win.block;
+    h->minb = win.minb;
+    h->grid = win.grid;
+    h->pipe = win.pipe;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(h)] = win;
+    return FPCLBM_OK;
 }
 
 }  // namespace
@@ -242,46 +385,38 @@ int fpclbm_create(fpclbm_t* out, int nx, int ny, int nz, int precision, int bc, 
         g_create_error = "unknown boundary condition";
         return FPCLBM_ERR_ARG;
     }
-    if (bc == FPCLBM_BC_WALLS_Y && ny < 1) {
-        g_create_error = "walls need ny >= 1";
-        return FPCLBM_ERR_ARG;
-    }
     fpclbm* h = new (std::nothrow) fpclbm();
     if (!h) {
         g_create_error = "host allocation failed";
         return FPCLBM_ERR_ALLOC;
     }
-    h->nx = nx;
-    h->ny = ny;
-    h->nz = nz;
-    h->ncells = (unsigned)n;
-    h->stride = (unsigned)stride;
+    Box b;
+    b.nx = nx;
+    b.ny = ny;
+    b.nz = nz;
+    b.ncells = (unsigned)n;
+    b.stride = (unsigned)stride;
+    h->boxes.push_back(b);
+    h->total_cells = n;
     h->precision = precision;
     h->bc = bc;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     rates_from_params(1.0, 0.0, h->omega);
-    cudaError_t e = cudaGetDevice(&h->device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_pop, 27ull * stride * elem_size(precision));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_part, sizeof(double) * 5 * (size_t)diag_blocks(h->ncells));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, sizeof(double) * 5);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_diag, sizeof(double) * 5);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-        g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
-        const int code = (e == cudaErrorMemoryAllocation) ? FPCLBM_ERR_ALLOC : FPCLBM_ERR_CUDA;
+    int rc = alloc_common(h);
+    if (rc == FPCLBM_OK) {
+        cudaError_t e = cudaMalloc(&h->d_pop, 27ull * stride * elem_size(precision));
+        if (e != cudaSuccess) {
+            g_create_error = std::string("populations: ") + cudaGetErrorString(e);
+            rc = FPCLBM_ERR_ALLOC;
+        }
+    }
+    if (rc != FPCLBM_OK) {
         fpclbm_destroy(h);
-        return code;
+        return rc;
     }
     *out = h;
     return FPCLBM_OK;
 }
-
-int fpclbm_create_ensemble(fpclbm_t* out, int n_boxes, const int* dims, const double* tau, int precision,
-                           void* cuda_stream);  // ensemble.cu
 
 int fpclbm_destroy(fpclbm_t h)
 {
@@ -295,6 +430,8 @@ int fpclbm_destroy(fpclbm_t h)
     if (h->d_diag) cudaFree(h->d_diag);
     if (h->h_diag) cudaFreeHost(h->h_diag);
     if (h->d_closure) cudaFree(h->d_closure);
+    if (h->d_ens_boxes) cudaFree(h->d_ens_boxes);
+    if (h->d_tile_box) cudaFree(h->d_tile_box);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return FPCLBM_OK;
@@ -312,25 +449,31 @@ int fpclbm_init_fields(fpclbm_t h, const double* rho, const double* ux, const do
     if (!h) return FPCLBM_ERR_ARG;
     h->err.clear();
     if (!rho || !ux || !uy || !uz) return fail(h, FPCLBM_ERR_ARG, "null field pointer");
-    const BoxGeom b = geom_of(h);
-    if (on_device) {
-        FPC_CK(h, launch_init_eq(h->precision, b, rho, ux, uy, uz, 0, h->ncells, h->stream), "init kernel");
-    } else {
-        const unsigned chunk = h->ncells < kChunk ? h->ncells : kChunk;
+    for (const Box& b : h->boxes) {
+        const BoxGeom g = geom_of(h, b);
+        if (on_device) {
+            FPC_CK(h,
+                   launch_init_eq(h->precision, g, rho + b.cell0, ux + b.cell0, uy + b.cell0, uz + b.cell0, 0,
+                                  b.ncells, h->stream),
+                   "init kernel");
+            continue;
+        }
+        const unsigned chunk = chunk_of(b);
         int rc = ensure_stage(h, sizeof(double) * 4 * (size_t)chunk);
         if (rc) return rc;
         double* d = h->d_stage;
-        for (unsigned c0 = 0; c0 < h->ncells; c0 += chunk) {
-            const unsigned n = (h->ncells - c0 < chunk) ? h->ncells - c0 : chunk;
+        for (unsigned c0 = 0; c0 < b.ncells; c0 += chunk) {
+            const unsigned n = (b.ncells - c0 < chunk) ? b.ncells - c0 : chunk;
             const size_t bytes = sizeof(double) * n;
-            FPC_CK(h, cudaMemcpyAsync(d, rho + c0, bytes, cudaMemcpyHostToDevice, h->stream), "copy rho");
-            FPC_CK(h, cudaMemcpyAsync(d + chunk, ux + c0, bytes, cudaMemcpyHostToDevice, h->stream), "copy ux");
-            FPC_CK(h, cudaMemcpyAsync(d + 2 * (size_t)chunk, uy + c0, bytes, cudaMemcpyHostToDevice, h->stream),
+            const size_t at = (size_t)b.cell0 + c0;
+            FPC_CK(h, cudaMemcpyAsync(d, rho + at, bytes, cudaMemcpyHostToDevice, h->stream), "copy rho");
+            FPC_CK(h, cudaMemcpyAsync(d + chunk, ux + at, bytes, cudaMemcpyHostToDevice, h->stream), "copy ux");
+            FPC_CK(h, cudaMemcpyAsync(d + 2 * (size_t)chunk, uy + at, bytes, cudaMemcpyHostToDevice, h->stream),
                    "copy uy");
-            FPC_CK(h, cudaMemcpyAsync(d + 3 * (size_t)chunk, uz + c0, bytes, cudaMemcpyHostToDevice, h->stream),
+            FPC_CK(h, cudaMemcpyAsync(d + 3 * (size_t)chunk, uz + at, bytes, cudaMemcpyHostToDevice, h->stream),
                    "copy uz");
             FPC_CK(h,
-                   launch_init_eq(h->precision, b, d, d + chunk, d + 2 * (size_t)chunk, d + 3 * (size_t)chunk, c0, n,
+                   launch_init_eq(h->precision, g, d, d + chunk, d + 2 * (size_t)chunk, d + 3 * (size_t)chunk, c0, n,
                                   h->stream),
                    "init kernel");
         }
@@ -351,13 +494,16 @@ int fpclbm_set_params(fpclbm_t h, double tau, double drift, int diffusion)
         return fail(h, FPCLBM_ERR_ARG, "tau and drift must be finite, drift >= 0");
     if (diffusion == FPCLBM_DIFF_FP_LEARNED && !h->have_closure)
         return fail(h, FPCLBM_ERR_STATE, "learned diffusion mode needs fpclbm_set_closure first");
+    if (diffusion == FPCLBM_DIFF_FP_LEARNED && h->ensemble)
+        return fail(h, FPCLBM_ERR_ARG, "learned diffusion mode is for single boxes");
     double om[27];
-    rates_from_params(tau, drift, om);
+    rates_from_params(h->ensemble ? 1.0 : tau, drift, om);
     std::string why;
     if (!rates_valid(om, why)) return fail(h, FPCLBM_ERR_PARAM, why);
     std::memcpy(h->omega, om, sizeof om);
     h->diffusion = diffusion;
     h->graph_valid = false;
+    h->tuned = false;
     return FPCLBM_OK;
 }
 
@@ -366,6 +512,7 @@ int fpclbm_set_rates(fpclbm_t h, const double omega[27])
     if (!h) return FPCLBM_ERR_ARG;
     h->err.clear();
     if (!omega) return fail(h, FPCLBM_ERR_ARG, "omega is NULL");
+    if (h->ensemble) return fail(h, FPCLBM_ERR_ARG, "set_rates is for single boxes");
     std::string why;
     if (!rates_valid(omega, why)) return fail(h, FPCLBM_ERR_PARAM, why);
     std::memcpy(h->omega, omega, sizeof(double) * 27);
@@ -383,6 +530,7 @@ int fpclbm_set_force(fpclbm_t h, double Fx, double Fy, double Fz)
     h->F[1] = Fy;
     h->F[2] = Fz;
     h->graph_valid = false;
+    h->tuned = false;
     return FPCLBM_OK;
 }
 
@@ -393,11 +541,16 @@ int fpclbm_step(fpclbm_t h, long long n)
     if (n < 0) return fail(h, FPCLBM_ERR_ARG, "negative step count");
     if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
     if (n == 0) return FPCLBM_OK;
+    if (!h->tuned) {
+        int rc = autotune(h);
+        if (rc) return rc;
+        h->graph_valid = false;
+    }
     FPC_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream), "flag reset");
     long long done = 0;
     // bring the AA parity to even with single launches
     while (done < n && ((h->steps + done) & 1)) {
-        FPC_CK(h, one_step(h, h->steps + done, h->stream), "step launch");
+        FPC_CK(h, one_step(h, h->steps + done, h->stream, h->block, h->minb, h->grid, h->pipe), "step launch");
         ++done;
     }
     if (n - done >= kGraphSteps) {
@@ -411,7 +564,7 @@ int fpclbm_step(fpclbm_t h, long long n)
         }
     }
     while (done < n) {
-        FPC_CK(h, one_step(h, h->steps + done, h->stream), "step launch");
+        FPC_CK(h, one_step(h, h->steps + done, h->stream, h->block, h->minb, h->grid, h->pipe), "step launch");
         ++done;
     }
     h->steps += n;
@@ -433,31 +586,36 @@ int fpclbm_moments(fpclbm_t h, double* rho, double* ux, double* uy, double* uz, 
     if (!h) return FPCLBM_ERR_ARG;
     h->err.clear();
     if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
-    const BoxGeom b = geom_of(h);
     const int parity = (int)(h->steps & 1);
-    if (on_device) {
-        FPC_CK(h,
-               launch_moments(h->precision, b, parity, h->F[0], h->F[1], h->F[2], rho, ux, uy, uz, 0, h->ncells,
-                              h->stream),
-               "moments kernel");
-    } else {
-        const unsigned chunk = h->ncells < kChunk ? h->ncells : kChunk;
+    double* outs[4] = {rho, ux, uy, uz};
+    for (const Box& b : h->boxes) {
+        const BoxGeom g = geom_of(h, b);
+        if (on_device) {
+            double* o[4];
+            for (int q = 0; q < 4; ++q) o[q] = outs[q] ? outs[q] + b.cell0 : nullptr;
+            FPC_CK(h,
+                   launch_moments(h->precision, g, parity, h->F[0], h->F[1], h->F[2], o[0], o[1], o[2], o[3], 0,
+                                  b.ncells, h->stream),
+                   "moments kernel");
+            continue;
+        }
+        const unsigned chunk = chunk_of(b);
         int rc = ensure_stage(h, sizeof(double) * 4 * (size_t)chunk);
         if (rc) return rc;
         double* d = h->d_stage;
-        double* outs[4] = {rho, ux, uy, uz};
-        for (unsigned c0 = 0; c0 < h->ncells; c0 += chunk) {
-            const unsigned n = (h->ncells - c0 < chunk) ? h->ncells - c0 : chunk;
+        for (unsigned c0 = 0; c0 < b.ncells; c0 += chunk) {
+            const unsigned n = (b.ncells - c0 < chunk) ? b.ncells - c0 : chunk;
             double* dd[4];
             for (int q = 0; q < 4; ++q) dd[q] = outs[q] ? d + (size_t)q * chunk : nullptr;
             FPC_CK(h,
-                   launch_moments(h->precision, b, parity, h->F[0], h->F[1], h->F[2], dd[0], dd[1], dd[2], dd[3], c0,
+                   launch_moments(h->precision, g, parity, h->F[0], h->F[1], h->F[2], dd[0], dd[1], dd[2], dd[3], c0,
                                   n, h->stream),
                    "moments kernel");
             for (int q = 0; q < 4; ++q)
                 if (outs[q])
                     FPC_CK(h,
-                           cudaMemcpyAsync(outs[q] + c0, dd[q], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream),
+                           cudaMemcpyAsync(outs[q] + b.cell0 + c0, dd[q], sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                           h->stream),
                            "copy moments");
         }
     }
@@ -471,10 +629,13 @@ int fpclbm_diagnostics(fpclbm_t h, double out[5])
     h->err.clear();
     if (!out) return fail(h, FPCLBM_ERR_ARG, "out is NULL");
     if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
-    FPC_CK(h,
-           launch_diagnostics(h->precision, geom_of(h), (int)(h->steps & 1), h->F[0], h->F[1], h->F[2], h->d_part,
-                              h->d_diag, h->stream),
-           "diagnostics kernels");
+    const int parity = (int)(h->steps & 1);
+    for (const Box& b : h->boxes)
+        FPC_CK(h,
+               launch_diag_partial(h->precision, geom_of(h, b), parity, h->F[0], h->F[1], h->F[2],
+                                   h->d_part + 5 * (size_t)b.diag0, h->stream),
+               "diagnostics kernel");
+    FPC_CK(h, launch_diag_final(h->d_part, (int)h->diag_parts, h->d_diag, h->stream), "diagnostics kernel");
     FPC_CK(h, cudaMemcpyAsync(h->h_diag, h->d_diag, sizeof(double) * 5, cudaMemcpyDeviceToHost, h->stream),
            "copy diagnostics");
     FPC_CK(h, cudaStreamSynchronize(h->stream), "diagnostics sync");
@@ -488,18 +649,22 @@ int fpclbm_get_populations(fpclbm_t h, double* f)
     h->err.clear();
     if (!f) return fail(h, FPCLBM_ERR_ARG, "f is NULL");
     if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
-    const unsigned chunk = h->ncells < kChunk ? h->ncells : kChunk;
-    int rc = ensure_stage(h, sizeof(double) * 27 * (size_t)chunk);
-    if (rc) return rc;
-    const BoxGeom b = geom_of(h);
     const int parity = (int)(h->steps & 1);
-    for (unsigned c0 = 0; c0 < h->ncells; c0 += chunk) {
-        const unsigned n = (h->ncells - c0 < chunk) ? h->ncells - c0 : chunk;
-        FPC_CK(h, launch_get_pops(h->precision, b, parity, h->d_stage, chunk, c0, n, h->stream), "populations kernel");
-        FPC_CK(h,
-               cudaMemcpy2DAsync(f + c0, sizeof(double) * h->ncells, h->d_stage, sizeof(double) * chunk,
-                                 sizeof(double) * n, 27, cudaMemcpyDeviceToHost, h->stream),
-               "copy populations");
+    const size_t pitch = sizeof(double) * h->total_cells;
+    for (const Box& b : h->boxes) {
+        const unsigned chunk = chunk_of(b);
+        int rc = ensure_stage(h, sizeof(double) * 27 * (size_t)chunk);
+        if (rc) return rc;
+        const BoxGeom g = geom_of(h, b);
+        for (unsigned c0 = 0; c0 < b.ncells; c0 += chunk) {
+            const unsigned n = (b.ncells - c0 < chunk) ? b.ncells - c0 : chunk;
+            FPC_CK(h, launch_get_pops(h->precision, g, parity, h->d_stage, chunk, c0, n, h->stream),
+                   "populations kernel");
+            FPC_CK(h,
+                   cudaMemcpy2DAsync(f + b.cell0 + c0, pitch, h->d_stage, sizeof(double) * chunk, sizeof(double) * n,
+                                     27, cudaMemcpyDeviceToHost, h->stream),
+                   "copy populations");
+        }
     }
     FPC_CK(h, cudaStreamSynchronize(h->stream), "populations sync");
     return FPCLBM_OK;
@@ -513,22 +678,41 @@ int fpclbm_get_populations_at(fpclbm_t h, const long long* cells, int n, double*
     if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
     if (n == 0) return FPCLBM_OK;
     if (n > (int)kChunk) return fail(h, FPCLBM_ERR_ARG, "at most 2^20 cells per call");
-    std::vector<unsigned> idx(n);
-    for (int i = 0; i < n; ++i) {
-        if (cells[i] < 0 || cells[i] >= (long long)h->ncells) return fail(h, FPCLBM_ERR_ARG, "cell index out of range");
-        idx[i] = (unsigned)cells[i];
-    }
+    for (int i = 0; i < n; ++i)
+        if (cells[i] < 0 || (unsigned long long)cells[i] >= h->total_cells)
+            return fail(h, FPCLBM_ERR_ARG, "cell index out of range");
     const size_t out_bytes = sizeof(double) * 27 * (size_t)n;
     const size_t idx_bytes = (sizeof(unsigned) * (size_t)n + 255) / 256 * 256;
-    int rc = ensure_stage(h, out_bytes + idx_bytes);
+    int rc = ensure_stage(h, 2 * out_bytes + idx_bytes);
     if (rc) return rc;
     double* d_out = h->d_stage;
-    unsigned* d_idx = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(h->d_stage) + out_bytes);
-    FPC_CK(h, cudaMemcpyAsync(d_idx, idx.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, h->stream), "copy cells");
-    FPC_CK(h, launch_get_pops_at(h->precision, geom_of(h), (int)(h->steps & 1), d_idx, (unsigned)n, d_out, h->stream),
-           "populations kernel");
-    FPC_CK(h, cudaMemcpyAsync(f, d_out, out_bytes, cudaMemcpyDeviceToHost, h->stream), "copy populations");
-    FPC_CK(h, cudaStreamSynchronize(h->stream), "populations sync");
+    unsigned* d_idx = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(h->d_stage) + 2 * out_bytes);
+    std::vector<double> host(27 * (size_t)n);
+    std::vector<unsigned> idx;
+    std::vector<int> which;
+    const int parity = (int)(h->steps & 1);
+    for (const Box& b : h->boxes) {
+        idx.clear();
+        which.clear();
+        for (int i = 0; i < n; ++i)
+            if ((unsigned long long)cells[i] >= b.cell0 && (unsigned long long)cells[i] < (unsigned long long)b.cell0 + b.ncells) {
+                idx.push_back((unsigned)(cells[i] - b.cell0));
+                which.push_back(i);
+            }
+        if (idx.empty()) continue;
+        const unsigned m = (unsigned)idx.size();
+        FPC_CK(h, cudaMemcpyAsync(d_idx, idx.data(), sizeof(unsigned) * m, cudaMemcpyHostToDevice, h->stream),
+               "copy cells");
+        FPC_CK(h, launch_get_pops_at(h->precision, geom_of(h, b), parity, d_idx, m, d_out, h->stream),
+               "populations kernel");
+        std::vector<double> part(27 * (size_t)m);
+        FPC_CK(h, cudaMemcpyAsync(part.data(), d_out, sizeof(double) * 27 * m, cudaMemcpyDeviceToHost, h->stream),
+               "copy populations");
+        FPC_CK(h, cudaStreamSynchronize(h->stream), "populations sync");
+        for (unsigned k = 0; k < m; ++k)
+            for (int a = 0; a < 27; ++a) host[(size_t)a * n + which[k]] = part[(size_t)a * m + k];
+    }
+    std::memcpy(f, host.data(), sizeof(double) * 27 * (size_t)n);
     return FPCLBM_OK;
 }
 
@@ -537,17 +721,20 @@ int fpclbm_set_populations(fpclbm_t h, const double* f)
     if (!h) return FPCLBM_ERR_ARG;
     h->err.clear();
     if (!f) return fail(h, FPCLBM_ERR_ARG, "f is NULL");
-    const unsigned chunk = h->ncells < kChunk ? h->ncells : kChunk;
-    int rc = ensure_stage(h, sizeof(double) * 27 * (size_t)chunk);
-    if (rc) return rc;
-    const BoxGeom b = geom_of(h);
-    for (unsigned c0 = 0; c0 < h->ncells; c0 += chunk) {
-        const unsigned n = (h->ncells - c0 < chunk) ? h->ncells - c0 : chunk;
-        FPC_CK(h,
-               cudaMemcpy2DAsync(h->d_stage, sizeof(double) * chunk, f + c0, sizeof(double) * h->ncells,
-                                 sizeof(double) * n, 27, cudaMemcpyHostToDevice, h->stream),
-               "copy populations");
-        FPC_CK(h, launch_set_pops(h->precision, b, h->d_stage, chunk, c0, n, h->stream), "populations kernel");
+    const size_t pitch = sizeof(double) * h->total_cells;
+    for (const Box& b : h->boxes) {
+        const unsigned chunk = chunk_of(b);
+        int rc = ensure_stage(h, sizeof(double) * 27 * (size_t)chunk);
+        if (rc) return rc;
+        const BoxGeom g = geom_of(h, b);
+        for (unsigned c0 = 0; c0 < b.ncells; c0 += chunk) {
+            const unsigned n = (b.ncells - c0 < chunk) ? b.ncells - c0 : chunk;
+            FPC_CK(h,
+                   cudaMemcpy2DAsync(h->d_stage, sizeof(double) * chunk, f + b.cell0 + c0, pitch, sizeof(double) * n,
+                                     27, cudaMemcpyHostToDevice, h->stream),
+                   "copy populations");
+            FPC_CK(h, launch_set_pops(h->precision, g, h->d_stage, chunk, c0, n, h->stream), "populations kernel");
+        }
     }
     FPC_CK(h, cudaStreamSynchronize(h->stream), "populations sync");
     h->initialized = true;

@@ -10,7 +10,9 @@ enum { P_FP64 = 0, P_FP32 = 1, P_FP16 = 2, P_BF16 = 3 };
 
 // Launch configuration of the single-box step kernel (autotuned).
 struct StepLaunch {
-    int block;  // threads per block
+    int block;     // threads per block (<= 256)
+    int minb = 2;  // register-cap variant: minimum resident blocks of 256 threads per SM (2, 3 or 4)
+    int pipe = 0;  // 1: software-pipelined persistent variant (cp.async prefetch), 4/8-byte storage only
 };
 
 // One time step of a single box.  odd selects the AA-pattern parity (0: own
@@ -44,10 +46,12 @@ cudaError_t launch_get_pops_at(int precision, const BoxGeom& b, int parity, cons
 // populations <- in[alpha * ld + (c - c0)] (full f, paper alpha order), natural parity
 cudaError_t launch_set_pops(int precision, const BoxGeom& b, const double* in, unsigned ld, unsigned c0, unsigned n,
                             cudaStream_t st);
-// fp64 diagnostics: partial sums per block into part[5 * nblocks], then out[5]
+// fp64 diagnostics: partial sums of (rho, rho u, rho |u|^2 / 2) per block of
+// diag_blocks(ncells) into part[5 * k], then one pass over all partials.
 int diag_blocks(unsigned ncells);
-cudaError_t launch_diagnostics(int precision, const BoxGeom& b, int parity, double Fx, double Fy, double Fz,
-                               double* part, double* out, cudaStream_t st);
+cudaError_t launch_diag_partial(int precision, const BoxGeom& b, int parity, double Fx, double Fy, double Fz,
+                                double* part, cudaStream_t st);
+cudaError_t launch_diag_final(const double* part, int nparts, double* out, cudaStream_t st);
 
 // Paper alpha order -> tensor slot (host table, filled from the velocity list).
 extern const int kSlotOfAlpha[27];

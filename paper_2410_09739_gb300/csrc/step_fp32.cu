@@ -1,0 +1,12 @@
+// step_fp32.cu -- step-kernel instantiations for float storage, float arithmetic.
+#include "step_kernel.cuh"
+
+namespace fpc {
+
+cudaError_t launch_step_fp32(int odd, int walls, int force, int mode, const StepArgs<float>& a, const StepLaunch& cfg,
+                          cudaStream_t st)
+{
+    return step_dispatch<float, float>(odd, walls, force, mode, a, cfg, st);
+}
+
+}  // namespace fpc

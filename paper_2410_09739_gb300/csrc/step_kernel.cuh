@@ -1,0 +1,185 @@
+// step_kernel.cuh -- fused collide-and-stream kernel of one box (AA pattern,
+// see cell.cuh): one thread per cell, one launch per time step.  MINB is the
+// minimum resident blocks per SM handed to __launch_bounds__, i.e. the
+// register cap (2: ~120, 3: ~80, 4: 64 registers); the autotuner times the
+// variants and keeps the fastest.
+#pragma once
+#include "cell.cuh"
+#include "internal.h"
+
+namespace fpc {
+
+template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step(const StepArgs<R> a)
+{
+    const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= a.ncells) return;
+    CellGeom G;
+    G.stride = a.stride;
+    G.nx = a.nx;
+    G.ny = a.ny;
+    G.nz = a.nz;
+    G.div_nx = a.div_nx;
+    G.div_nxny = a.div_nxny;
+    const Rates<R>& rt = a.rates;
+    update_cell<S, R, ODD, WALLS, FORCE, MODE>(static_cast<S*>(a.buf), G, cell, rt, a.Fx, a.Fy, a.Fz, rt.om[4],
+                                               rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.closure, a.flag);
+}
+
+// ---------------------------------------------------------------------------
+// Software-pipelined variant: a persistent grid walks tiles of blockDim cells;
+// while a thread collides its cell of tile t, the 27 loads of its cell of the
+// next tile are already in flight as cp.async copies into the thread's own
+// column of a two-stage shared-memory buffer [2][27][blockDim].  Bytes in
+// flight no longer cost registers, so the load and compute phases of a warp
+// overlap.  Each thread reads back only what it copied itself, so a per-thread
+// cp.async.wait_group is the only synchronisation.  Storage of 4 or 8 bytes.
+// ---------------------------------------------------------------------------
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_step_pipe(const StepArgs<R> a, unsigned ntiles)
+{
+    static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async moves 4, 8 or 16 bytes");
+    extern __shared__ __align__(16) unsigned char fpc_smem[];
+    S* sm = reinterpret_cast<S*>(fpc_smem);
+    const unsigned T = blockDim.x, tid = threadIdx.x;
+    CellGeom G;
+    G.stride = a.stride;
+    G.nx = a.nx;
+    G.ny = a.ny;
+    G.nz = a.nz;
+    G.div_nx = a.div_nx;
+    G.div_nxny = a.div_nxny;
+    S* __restrict__ buf = static_cast<S*>(a.buf);
+    const unsigned stride = a.stride;
+    const Rates<R>& rt = a.rates;
+
+    auto issue = [&](unsigned tile, int stage) {
+        const unsigned cell = tile * T + tid;
+        if (tile < ntiles && cell < a.ncells) {
+            Nbr n;
+            if (ODD) n = make_nbr<WALLS>(G, cell);
+            S* dst = sm + (size_t)stage * 27 * T + tid;
+#pragma unroll
+            for (int s = 0; s < 27; ++s)
+                cp_async<sizeof(S)>(dst + s * T, buf + (size_t)load_off<ODD, WALLS>(s, n, stride, cell));
+        }
+        cp_async_commit();
+    };
+
+    int stage = 0;
+    unsigned t = blockIdx.x;
+    issue(t, 0);
+    for (; t < ntiles; t += gridDim.x) {
+        issue(t + gridDim.x, stage ^ 1);
+        cp_async_wait<1>();
+        const unsigned cell = t * T + tid;
+        if (cell < a.ncells) {
+            R g[27];
+            const S* src = sm + (size_t)stage * 27 * T + tid;
+#pragma unroll
+            for (int s = 0; s < 27; ++s) g[s] = Store<S>::ld(src + s * T);
+            const bool ok = collide_cell<R, FORCE, MODE>(g, rt, a.Fx, a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6],
+                                                         rt.om[8], rt.om[9], a.closure);
+            if (!ok) atomicOr(a.flag, 1);
+            Nbr n;
+            if (ODD) n = make_nbr<WALLS>(G, cell);
+#pragma unroll
+            for (int s = 0; s < 27; ++s) Store<S>::st(buf + (size_t)store_off<ODD, WALLS>(s, n, stride, cell), g[s]);
+        }
+        stage ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
+{
+    constexpr int T = 128;
+    const size_t smem = 2ull * 27 * T * sizeof(S);
+    auto kern = k_step_pipe<S, R, ODD, WALLS, FORCE, MODE, 2 * MINB>;
+    static int per_sm = 0, sms = 0;  // benign race: every thread computes the same values
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, T, smem) != cudaSuccess || n < 1) n = 1;
+        per_sm = n;
+    }
+    const unsigned ntiles = (a.ncells + T - 1) / T;
+    unsigned grid = (unsigned)(per_sm * sms);
+    if (grid > ntiles) grid = ntiles;
+    kern<<<grid, T, smem, st>>>(a, ntiles);
+    return cudaGetLastError();
+}
+
+template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
+{
+    if constexpr (sizeof(S) >= 4) {
+        if (cfg.pipe) return step_go_pipe<S, R, ODD, WALLS, FORCE, MODE, MINB>(a, st);
+    }
+    const int block = cfg.block > 0 ? cfg.block : 256;
+    const unsigned grid = (a.ncells + block - 1) / block;
+    k_step<S, R, ODD, WALLS, FORCE, MODE, MINB><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Register-cap variants exist for the fp32-arithmetic FP and EQ modes; fp64
+// and the learned mode have one variant each.
+template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE>
+cudaError_t step_by_minb(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
+{
+    constexpr bool tunable = sizeof(R) == 4 && MODE != MODE_LEARNED;
+    if constexpr (tunable) {
+        if (cfg.minb == 3) return step_go<S, R, ODD, WALLS, FORCE, MODE, 3>(a, cfg, st);
+        if (cfg.minb == 4) return step_go<S, R, ODD, WALLS, FORCE, MODE, 4>(a, cfg, st);
+        return step_go<S, R, ODD, WALLS, FORCE, MODE, 2>(a, cfg, st);
+    } else {
+        return step_go<S, R, ODD, WALLS, FORCE, MODE, 1>(a, cfg, st);
+    }
+}
+
+template <typename S, typename R, bool ODD, bool WALLS, bool FORCE>
+cudaError_t step_by_mode(int mode, const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
+{
+    switch (mode) {
+        case MODE_FP: return step_by_minb<S, R, ODD, WALLS, FORCE, MODE_FP>(a, cfg, st);
+        case MODE_EQ: return step_by_minb<S, R, ODD, WALLS, FORCE, MODE_EQ>(a, cfg, st);
+        case MODE_LEARNED: return step_by_minb<S, R, ODD, WALLS, FORCE, MODE_LEARNED>(a, cfg, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename S, typename R>
+cudaError_t step_dispatch(int odd, int walls, int force, int mode, const StepArgs<R>& a, const StepLaunch& cfg,
+                          cudaStream_t st)
+{
+    if (odd) {
+        if (walls) return force ? step_by_mode<S, R, true, true, true>(mode, a, cfg, st)
+                                : step_by_mode<S, R, true, true, false>(mode, a, cfg, st);
+        return force ? step_by_mode<S, R, true, false, true>(mode, a, cfg, st)
+                     : step_by_mode<S, R, true, false, false>(mode, a, cfg, st);
+    }
+    if (walls) return force ? step_by_mode<S, R, false, true, true>(mode, a, cfg, st)
+                            : step_by_mode<S, R, false, true, false>(mode, a, cfg, st);
+    return force ? step_by_mode<S, R, false, false, true>(mode, a, cfg, st)
+                 : step_by_mode<S, R, false, false, false>(mode, a, cfg, st);
+}
+
+}  // namespace fpc

@@ -156,3 +156,20 @@ def ensemble_config(n_boxes: int = 256, seed: int = 2410, tau_lo: float = 0.505,
     sides = rng.choice(np.array(ENSEMBLE_SIDES), size=n_boxes)
     taus = rng.uniform(tau_lo, tau_hi, size=n_boxes)
     return [int(s) for s in sides], [float(t) for t in taus]
+
+
+def ensemble_fields(sides, seed: int = 2410):
+    """Initial fields of an ensemble: one seeded solenoidal field per distinct side, and for every
+    box a random periodic shift and axis permutation of it (both keep the field divergence-free
+    and its spectrum), so that boxes differ without one FFT per box."""
+    rng = np.random.default_rng(seed)
+    base = {s: solenoidal_field(s, seed + s) for s in sorted(set(sides))}
+    out = []
+    for s in sides:
+        rho, ux, uy, uz = base[s]
+        perm = rng.permutation(3)                # new axis order (z, y, x) <- old
+        shift = tuple(int(v) for v in rng.integers(0, s, 3))
+        comps = [uz, uy, ux]                      # component along array axis 0, 1, 2
+        moved = [np.roll(np.transpose(comps[perm[i]], perm), shift, axis=(0, 1, 2)) for i in range(3)]
+        out.append((np.ones((s, s, s)), moved[2], moved[1], moved[0]))
+    return out
