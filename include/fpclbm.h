@@ -140,6 +140,31 @@ FPCLBM_API int fpclbm_moments(fpclbm_t h, double* rho, double* ux, double* uy, d
  * Errors: ARG, STATE, CUDA. */
 FPCLBM_API int fpclbm_diagnostics(fpclbm_t h, double out[5]);
 
+/* The diagnostics of fpclbm_diagnostics for callers that cannot allocate
+ * device memory (no counterpart in the paper).  Some callers must not call
+ * cudaMalloc: code embedded in a host application that owns every device
+ * allocation through its own pool or arena, or a loop whose latency budget
+ * forbids the synchronisation that allocating and freeing imply.  This entry
+ * point allocates nothing and needs no handle:
+ *   f       device pointer, full populations, double, alpha-major
+ *           f[alpha * ncells + cell] in the paper's alpha order (the layout of
+ *           fpclbm_get_populations);
+ *   ncells  1 .. FPCLBM_NOALLOC_MAX_CELLS, else ARG;
+ *   Fx..Fz  body force, for the half-force velocity of Step 7;
+ *   out     device pointer to 5 doubles: sum rho, sum rho u (3), sum rho|u|^2/2;
+ *   cuda_stream  stream to run on (NULL = legacy default stream); the call
+ *           does not synchronise it.
+ * Its block partials live in a fixed device array inside the library (40 KB
+ * on every device that loads it, kept until the process exits).  The first
+ * call on a device looks up that array's device address with the device
+ * current and caches it: make that first call before any stream capture.
+ * Calls share the array; each overwrites the partials it reads, so nothing
+ * needs clearing, but calls that overlap on the GPU race -- order them on one
+ * stream.  Errors: ARG, CUDA (text via fpclbm_last_error(NULL)). */
+#define FPCLBM_NOALLOC_MAX_CELLS 2147483647LL
+FPCLBM_API int fpclbm_diagnostics_noalloc(const double* f, long long ncells, double Fx, double Fy, double Fz,
+                                          double* out, void* cuda_stream);
+
 /* Copy out / in all populations as full f (not deviations), double,
  * alpha-major in the paper's alpha order, host memory.  get works at any
  * step parity; set leaves the handle at step 0 of a new run.

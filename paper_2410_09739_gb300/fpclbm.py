@@ -47,7 +47,7 @@ PRECISIONS = {"fp64": FPCLBM_FP64, "fp32": FPCLBM_FP32, "fp16": FPCLBM_FP32_STOR
 EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fpclbm_set_params",
             "fpclbm_set_rates", "fpclbm_set_force", "fpclbm_step", "fpclbm_moments", "fpclbm_diagnostics",
             "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_set_closure",
-            "fpclbm_destroy", "fpclbm_last_error")
+            "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc")
 
 
 class FpclbmError(RuntimeError):
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     L.fpclbm_set_populations.argtypes = [_P, _P]
     L.fpclbm_get_step_count.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong)]
     L.fpclbm_set_closure.argtypes = [_P, ctypes.POINTER(ctypes.c_ushort), ctypes.c_int]
+    L.fpclbm_diagnostics_noalloc.argtypes = [_P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, _P, _P]
     L.fpclbm_destroy.argtypes = [_P]
     L.fpclbm_last_error.argtypes = [_P]
     L.fpclbm_last_error.restype = ctypes.c_char_p
@@ -200,6 +202,15 @@ def fpclbm_get_step_count(h) -> int:
 def fpclbm_set_closure(h, bf16_bits):
     w = np.ascontiguousarray(np.asarray(bf16_bits, dtype=np.uint16))
     return _check(h, load().fpclbm_set_closure(h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_ushort)), w.size))
+
+
+def fpclbm_diagnostics_noalloc(f_dev, ncells: int, Fx: float, Fy: float, Fz: float, out_dev, stream: int = 0):
+    """Diagnostics of full populations already on the device, without any allocation by the
+    library: f_dev is a CUDA float64 tensor [27 * ncells] (alpha-major), out_dev a CUDA float64
+    tensor of 5.  Runs on `stream` (a cudaStream_t handle, 0 = default) and does not synchronise."""
+    rc = load().fpclbm_diagnostics_noalloc(_ptr(f_dev, 1), int(ncells), float(Fx), float(Fy), float(Fz),
+                                           _ptr(out_dev, 1), _P(stream) if stream else None)
+    return _check(None, rc)
 
 
 def fpclbm_destroy(h):
