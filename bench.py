@@ -95,13 +95,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
+STEP_KERNEL_SOURCES = ("common.cuh", "collide.cuh", "closure.cuh", "cell.cuh", "step_kernel.cuh", "step_fp32.cu",
+                       "step_fp16.cu", "step_bf16.cu", "step_fp64.cu", "step_kernels.cu", "internal.h")
+
+
 def kernel_source_hash():
+    """Hash of the sources that define the single-box step kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2410_09739_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 

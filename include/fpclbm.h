@@ -191,6 +191,53 @@ FPCLBM_API int fpclbm_get_step_count(fpclbm_t h, long long* steps);
  * Errors: ARG. */
 FPCLBM_API int fpclbm_set_closure(fpclbm_t h, const unsigned short* bf16_weights, int n_params);
 
+/* Training data for the learned closure from a fine single box (no
+ * counterpart in the paper).  The box is cut into r x r x r blocks ("coarse
+ * cells", x fastest; nx, ny, nz multiples of r; ny / r >= 2 with walls).  Per
+ * coarse cell c it writes 9 features X[9 c + k] and a label T[c] (float;
+ * device pointers when on_device = 1, else host):
+ *   features  the non-equilibrium second-order central moments that a coarse
+ *             FPC-LBM with shear relaxation time tau_coarse carries for the
+ *             filtered flow, -2 rho cs^2 tau_coarse S_ij for ij = xx, yy, zz,
+ *             xy, xz, yz (Appendix C, Eq. noneqmmoments3D, with the discrete
+ *             1/omega -> tau), followed by the filtered velocity (3);
+ *   label     the shear-rate change that adds the sub-filter eddy viscosity:
+ *             1/((nu + nu_t)/cs^2 + 1/2) - 1/(nu/cs^2 + 1/2),
+ *             nu = cs^2 (tau_coarse - 1/2) (Eq. transportcoeff3DFPCLBM),
+ *             nu_t = max(0, -tau^d_ij S_ij / (2 S_kl S_kl)),
+ *             tau_ij = <u_i u_j> - <u_i><u_j>.
+ * <.> is the plain mean over the r^3 fine cells (rho, Step 7 velocity u,
+ * u_i u_j); S_ij is the strain rate of <u> by central differences in coarse
+ * cells (periodic in x, z; one-sided next to y walls).  Lattice velocities are
+ * unchanged under acoustic scaling (dt/dx fixed), so features and labels are
+ * in coarse lattice units.  Errors: ARG, STATE, ALLOC, CUDA. */
+FPCLBM_API int fpclbm_closure_sample(fpclbm_t fine, int r, double tau_coarse, float* X, float* T, int on_device);
+
+/* Train the closure network (layout of fpclbm_set_closure) on n samples,
+ * device arrays X[n][9] and T[n], by Adam (learning rate lr, beta 0.9/0.999)
+ * on the mean squared error for `epochs` passes in mini-batches of `batch`,
+ * each epoch in a fresh pseudo-random order; initial weights are drawn from
+ * `seed`.  Inputs and target are standardised during training; the weights
+ * written to out_bf16 (4865 bf16 bit patterns, host) have the
+ * standardisation folded into W1, b1, W3, b3, so fpclbm_set_closure applies
+ * them to raw inputs.  The forward and backward kernels use the bf16 weights
+ * with fp32 accumulation; fp32 master weights and gradients; the loss is
+ * accumulated in fp64.  loss_per_epoch (host, may be NULL) receives each
+ * epoch's mean squared error in standardised units.  Allocates its own
+ * device buffers for the call.  No counterpart in the paper.
+ * Errors: ARG, ALLOC, CUDA (text via fpclbm_last_error(NULL)). */
+FPCLBM_API int fpclbm_closure_train(const float* X, const float* T, long long n, int epochs, int batch, double lr,
+                                    unsigned long long seed, unsigned short* out_bf16, double* loss_per_epoch,
+                                    void* cuda_stream);
+
+/* One evaluation of the closure network's mean squared error on n samples
+ * (device arrays X[n][9], T[n], raw units) with the given bf16 weights (host):
+ * loss (host, fp64) and its gradient (host, 4865 fp32 values in the weight
+ * layout), computed by the training kernels.  For checking them against an
+ * fp64 reference.  Errors: ARG, ALLOC, CUDA. */
+FPCLBM_API int fpclbm_closure_grad(const float* X, const float* T, int n, const unsigned short* bf16_weights,
+                                   float* grad, double* loss, void* cuda_stream);
+
 /* Release everything the handle owns.  NULL is a no-op.  Returns OK. */
 FPCLBM_API int fpclbm_destroy(fpclbm_t h);
 

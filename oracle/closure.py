@@ -138,6 +138,33 @@ def box_filter(field, r: int):
     return a.reshape(nz // r, r, ny // r, r, nx // r, r).mean(axis=(1, 3, 5))
 
 
+def sample(rho, ux, uy, uz, r: int, tau_c: float, walls_y: bool, cs2: float = 1.0 / 3.0):
+    """Features [nc, 9] and labels [nc] of r^3 box-filtered fine fields (x fastest).
+
+    features: -2 rho cs2 tau_c S_ij (ij = xx, yy, zz, xy, xz, yz) of the filtered velocity (the
+    coarse non-equilibrium second moments of Appendix C Eq. noneqmmoments3D with 1/omega -> tau),
+    then the filtered velocity; label: delta_omega_label(cs2 (tau_c - 1/2), nu_t)."""
+    f = [np.asarray(a, dtype=np.float64) for a in (rho, ux, uy, uz)]
+    rb = box_filter(f[0], r)
+    ub = [box_filter(c, r) for c in f[1:]]
+    uu = {(i, j): box_filter(f[1 + i] * f[1 + j], r) for i in range(3) for j in range(i, 3)}
+    nut = eddy_viscosity(ub, uu, walls_y=walls_y)
+    axes = {0: 2, 1: 1, 2: 0}
+
+    def ddx(g, d):
+        if d == 1 and walls_y:
+            return np.gradient(g, axis=1)
+        return 0.5 * (np.roll(g, -1, axis=axes[d]) - np.roll(g, 1, axis=axes[d]))
+
+    grad = [[ddx(ub[i], j) for j in range(3)] for i in range(3)]
+    S = [[0.5 * (grad[i][j] + grad[j][i]) for j in range(3)] for i in range(3)]
+    pre = -2.0 * rb * cs2 * tau_c
+    X = np.stack([pre * S[0][0], pre * S[1][1], pre * S[2][2], pre * S[0][1], pre * S[0][2], pre * S[1][2],
+                  ub[0], ub[1], ub[2]], axis=-1).reshape(-1, 9)
+    T = delta_omega_label(cs2 * (tau_c - 0.5), nut, cs2).reshape(-1)
+    return X, T
+
+
 def eddy_viscosity(ubar, uu_bar, walls_y: bool = True):
     """nu_t = max(0, -tau^d_ij S_ij / (2 S_kl S_kl)) on the filtered grid.
 

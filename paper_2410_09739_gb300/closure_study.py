@@ -1,0 +1,199 @@
+"""Learned-closure study: coarse-grid FPC-LBM with the learned shear-rate correction
+against the plain coarse run and the box-filtered fine run of the same channel.
+
+Steps (all simulation, filtering and training on the GPU through the C ABI):
+  1. fine channel (walls in y, body force F = u*^2 / H, Re_tau = u* H / nu), spin-up;
+  2. during a collection window: every `snap` friction times, filter the fine
+     state onto r^3 blocks (fpclbm_closure_sample: features + eddy-viscosity
+     labels) and accumulate the fine mean velocity profile U(y);
+  3. train the closure network on the collected samples (fpclbm_closure_train);
+  4. coarse runs (acoustic scaling: dx, dt x r, nu / r, F x r), started from the
+     filtered fine velocity at the start of the window, over the same physical
+     time, plain FPC-LBM and FPC-LBM + closure, accumulating U(y);
+  5. L2-relative profile error of each coarse run against the filtered fine
+     profile, and the wall-clock speed-up of the coarse run over the fine run
+     for equal physical time on the same GPU.
+
+Usage: python -m paper_2410_09739_gb300.closure_study [--fine 384 192 192] [--r 4] ...
+Prints one JSON object.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+import workloads as W  # noqa: E402
+from paper_2410_09739_gb300 import fpclbm as F  # noqa: E402
+
+
+def parse(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--fine", type=int, nargs=3, default=(384, 192, 192), help="fine nx ny nz (ny = 2H)")
+    p.add_argument("--r", type=int, default=4, help="coarsening factor")
+    p.add_argument("--re-tau", type=float, default=395.0)
+    p.add_argument("--u-star", type=float, default=0.005)
+    p.add_argument("--spinup", type=float, default=20.0, help="fine spin-up in friction times H/u*")
+    p.add_argument("--collect", type=float, default=10.0, help="collection window in friction times")
+    p.add_argument("--snap", type=float, default=0.5, help="friction times between training snapshots")
+    p.add_argument("--epochs", type=int, default=30)
+    p.add_argument("--batch", type=int, default=1024)
+    p.add_argument("--lr", type=float, default=2e-3)
+    p.add_argument("--precision", default="bf16")
+    p.add_argument("--seed", type=int, default=7)
+    return p.parse_args(argv)
+
+
+class Profile:
+    """Running mean of U(y) = <u_x> over x, z and time (device tensors, host result)."""
+
+    def __init__(self, torch, shape):
+        self.torch = torch
+        self.shape = shape
+        self.sum = None
+        self.n = 0
+        n = shape[0] * shape[1] * shape[2]
+        self.buf = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
+
+    def add(self, lat):
+        F.fpclbm_moments(lat.h, *self.buf, on_device=1)
+        ux = self.buf[1].view(*self.shape)  # [nz, ny, nx]
+        p = ux.mean(dim=(0, 2))
+        self.sum = p if self.sum is None else self.sum + p
+        self.n += 1
+
+    def mean(self):
+        return (self.sum / self.n).cpu().numpy()
+
+
+def run(args):
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    nxf, nyf, nzf = args.fine
+    r = args.r
+    Hf = nyf / 2.0
+    us = args.u_star
+    nu_f = us * Hf / args.re_tau
+    tau_f = 3.0 * nu_f + 0.5
+    Ff = us * us / Hf
+    Tf = Hf / us  # fine steps per friction time
+    nxc, nyc, nzc = nxf // r, nyf // r, nzf // r
+    nu_c = nu_f / r
+    tau_c = 3.0 * nu_c + 0.5
+    Fc = Ff * r
+    Tc = Tf / r
+    out = {"config": {"fine": [nxf, nyf, nzf], "coarse": [nxc, nyc, nzc], "r": r, "re_tau": args.re_tau,
+                      "u_star": us, "tau_fine": tau_f, "tau_coarse": tau_c, "F_fine": Ff, "F_coarse": Fc,
+                      "friction_time_fine_steps": Tf, "precision": args.precision,
+                      "spinup_T": args.spinup, "collect_T": args.collect, "snap_T": args.snap}}
+
+    # 1. fine spin-up
+    fine = F.Lattice(nxf, nyf, nzf, args.precision, F.FPCLBM_BC_WALLS_Y, stream=stream)
+    fine.set_params(tau_f)
+    fine.set_force(Ff, 0.0, 0.0)
+    fine.init_fields(*W.channel_fields(nxf, nyf, nzf, us, seed=args.seed))
+    n_spin = int(round(args.spinup * Tf))
+    t0 = time.perf_counter()
+    done = 0
+    while done < n_spin:
+        k = min(4096, n_spin - done)
+        fine.step(k)
+        done += k
+    spin_s = time.perf_counter() - t0
+
+    # 2. collection window
+    nc = nxc * nyc * nzc
+    n_snap = max(1, int(round(args.collect / args.snap)))
+    X = torch.empty((n_snap * nc, 9), dtype=torch.float32, device="cuda")
+    T = torch.empty(n_snap * nc, dtype=torch.float32, device="cuda")
+    snap_steps = int(round(args.snap * Tf))
+    prof_f = Profile(torch, (nzf, nyf, nxf))
+    X0 = None
+    fine_steps = 0
+    fine_s = 0.0
+    for s in range(n_snap):
+        F.fpclbm_closure_sample(fine.h, r, tau_c, X[s * nc:(s + 1) * nc], T[s * nc:(s + 1) * nc], on_device=1)
+        if s == 0:
+            X0 = X[:nc].clone()
+        prof_f.add(fine)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fine.step(snap_steps)
+        fine_s += time.perf_counter() - t0
+        fine_steps += snap_steps
+    prof_f.add(fine)
+    U_fine = prof_f.mean().reshape(nyc, r).mean(axis=1)  # filtered onto coarse rows
+    fine.close()
+
+    # 3. training
+    t0 = time.perf_counter()
+    w, losses = F.fpclbm_closure_train(X, T, n_snap * nc, args.epochs, args.batch, args.lr, seed=args.seed,
+                                       stream=stream)
+    train_s = time.perf_counter() - t0
+    labels = T.cpu().numpy()
+    out["training"] = {"samples": n_snap * nc, "epochs": args.epochs, "loss_first": float(losses[0]),
+                       "loss_last": float(losses[-1]), "seconds": train_s,
+                       "label_mean": float(labels.mean()), "label_min": float(labels.min())}
+
+    # 4. coarse runs from the filtered velocity at the start of the window
+    u0 = X0[:, 6:9].double().cpu().numpy()
+    fields = (np.ones(nc), np.ascontiguousarray(u0[:, 0]), np.ascontiguousarray(u0[:, 1]),
+              np.ascontiguousarray(u0[:, 2]))
+    n_coarse = int(round(n_snap * args.snap * Tc))
+    coarse_res = {}
+    for name in ("plain", "learned"):
+        lat = F.Lattice(nxc, nyc, nzc, args.precision, F.FPCLBM_BC_WALLS_Y, stream=stream)
+        if name == "learned":
+            lat.set_closure(w)
+            lat.set_params(tau_c, 0.0, F.FPCLBM_DIFF_FP_LEARNED)
+        else:
+            lat.set_params(tau_c)
+        lat.set_force(Fc, 0.0, 0.0)
+        lat.init_fields(*fields)
+        prof = Profile(torch, (nzc, nyc, nxc))
+        per = max(1, int(round(args.snap * Tc)))
+        status, secs, steps = "ok", 0.0, 0
+        try:
+            for s in range(n_snap):
+                prof.add(lat)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lat.step(per)
+                secs += time.perf_counter() - t0
+                steps += per
+            prof.add(lat)
+            U = prof.mean()
+            err = float(np.linalg.norm(U - U_fine) / np.linalg.norm(U_fine))
+        except F.FpclbmError as e:
+            status, U, err = "diverged after %d steps (%s)" % (steps, e), None, None
+        coarse_res[name] = {"status": status, "profile_l2_rel_error": err, "steps": steps, "seconds": secs,
+                            "U": None if U is None else [float(v) for v in U]}
+        lat.close()
+    out["U_fine_filtered"] = [float(v) for v in U_fine]
+    out["coarse"] = coarse_res
+    # 5. speed-up for equal physical time (per friction time)
+    fine_per_T = fine_s / (fine_steps / Tf)
+    for name, res in coarse_res.items():
+        if res["steps"]:
+            res["speedup_vs_fine"] = fine_per_T / (res["seconds"] / (res["steps"] / Tc))
+    out["fine"] = {"spinup_seconds": spin_s, "collect_seconds": fine_s, "collect_steps": fine_steps,
+                   "seconds_per_friction_time": fine_per_T}
+    return out
+
+
+def main(argv=None):
+    args = parse(argv)
+    print(json.dumps(run(args)))
+
+
+if __name__ == "__main__":
+    main()

@@ -60,24 +60,26 @@ __device__ __forceinline__ Nbr make_nbr(const CellGeom& G, unsigned cell)
     return n;
 }
 
-// Element offset read for slot s (the population that streams into the cell).
-template <bool ODD, bool WALLS>
-__device__ __forceinline__ unsigned load_off(int s, const Nbr& n, unsigned stride, unsigned cell)
+// Address read for slot s (the population that streams into the cell).  The
+// slot row base buf + row * stride is the same for the whole warp, so it is
+// formed separately from the per-thread cell offset (uniform-register base).
+template <typename S, bool ODD, bool WALLS>
+__device__ __forceinline__ S* load_ptr(S* buf, int s, const Nbr& n, unsigned stride, unsigned cell)
 {
-    if (!ODD) return s * stride + cell;
+    if (!ODD) return buf + (size_t)s * stride + cell;
     const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
-    if (WALLS && !n.yin[iy]) return s * stride + cell;
-    return (26 - s) * stride + n.xs[ix] + n.yr[iy] + n.zp[iz];
+    if (WALLS && !n.yin[iy]) return buf + (size_t)s * stride + cell;
+    return buf + (size_t)(26 - s) * stride + (n.xs[ix] + n.yr[iy] + n.zp[iz]);
 }
 
-// Element offset written for slot s (the destination of the post-collision value).
-template <bool ODD, bool WALLS>
-__device__ __forceinline__ unsigned store_off(int s, const Nbr& n, unsigned stride, unsigned cell)
+// Address written for slot s (the destination of the post-collision value).
+template <typename S, bool ODD, bool WALLS>
+__device__ __forceinline__ S* store_ptr(S* buf, int s, const Nbr& n, unsigned stride, unsigned cell)
 {
-    if (!ODD) return (26 - s) * stride + cell;
+    if (!ODD) return buf + (size_t)(26 - s) * stride + cell;
     const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
-    if (WALLS && !n.yin[2 - iy]) return (26 - s) * stride + cell;
-    return s * stride + n.xs[2 - ix] + n.yr[2 - iy] + n.zp[2 - iz];
+    if (WALLS && !n.yin[2 - iy]) return buf + (size_t)(26 - s) * stride + cell;
+    return buf + (size_t)s * stride + (n.xs[2 - ix] + n.yr[2 - iy] + n.zp[2 - iz]);
 }
 
 template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE>
@@ -90,13 +92,13 @@ __device__ __forceinline__ void update_cell(S* __restrict__ buf, const CellGeom&
     Nbr n;
     if (ODD) n = make_nbr<WALLS>(G, cell);
 #pragma unroll
-    for (int s = 0; s < 27; ++s) g[s] = Store<S>::ld(buf + (size_t)load_off<ODD, WALLS>(s, n, stride, cell));
+    for (int s = 0; s < 27; ++s) g[s] = Store<S>::ld(load_ptr<S, ODD, WALLS>(buf, s, n, stride, cell));
 
     const bool ok = collide_cell<R, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, closure);
     if (!ok) atomicOr(flag, 1);
 
 #pragma unroll
-    for (int s = 0; s < 27; ++s) Store<S>::st(buf + (size_t)store_off<ODD, WALLS>(s, n, stride, cell), g[s]);
+    for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, WALLS>(buf, s, n, stride, cell), g[s]);
 }
 
 }  // namespace fpc

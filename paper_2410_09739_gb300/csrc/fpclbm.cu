@@ -252,14 +252,57 @@ struct TuneChoice {
     int block, minb, grid, pipe;
 };
 
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+
 bool verbose()
 {
     const char* v = std::getenv("FPCLBM_VERBOSE");
     return v && v[0] && v[0] != '0';
 }
 
-std::mutex g_tune_mu;
-std::map<std::string, TuneChoice> g_tune_cache;
+// Optional persistent cache of tuning results (FPCLBM_TUNE_CACHE = path): one
+// line "key block minb grid pipe" per configuration.  A run can reuse the
+// choice of an earlier run, e.g. a profiler run that must time the same
+// kernel variant as the plain run it profiles.
+void load_tune_file()
+{
+    static bool loaded = false;
+    if (loaded) return;
+    loaded = true;
+    const char* path = std::getenv("FPCLBM_TUNE_CACHE");
+    if (!path || !path[0]) return;
+    FILE* fp = std::fopen(path, "r");
+    if (!fp) return;
+    char key[200];
+    TuneChoice c;
+    while (std::fscanf(fp, "%199s %d %d %d %d", key, &c.block, &c.minb, &c.grid, &c.pipe) == 5)
+        g_tune_cache[key] = c;
+    std::fclose(fp);
+}
+
+void save_tune_file()
+{
+    const char* path = std::getenv("FPCLBM_TUNE_CACHE");
+    if (!path || !path[0]) return;
+    FILE* fp = std::fopen(path, "w");
+    if (!fp) return;
+    for (const auto& kv : g_tune_cache)
+        std::fprintf(fp, "%s %d %d %d %d\n", kv.first.c_str(), kv.second.block, kv.second.minb, kv.second.grid,
+                     kv.second.pipe);
+    std::fclose(fp);
+}
+
+// FPCLBM_LAUNCH = "block:minb:pipe" forces a single-box launch configuration.
+bool forced_launch(TuneChoice& c)
+{
+    const char* v = std::getenv("FPCLBM_LAUNCH");
+    if (!v || !v[0]) return false;
+    int b = 0, m = 0, p = 0;
+    if (std::sscanf(v, "%d:%d:%d", &b, &m, &p) != 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4) return false;
+    c = {b, m, 0, p ? 1 : 0};
+    return true;
+}
 
 std::string tune_key(const fpclbm* h)
 {
@@ -290,8 +333,19 @@ int autotune(fpclbm* h)
         for (int block : {128, 256}) cands.push_back({block, 1, 0, 0});
         if (pipe_ok && mode_of(h) != MODE_LEARNED) cands.push_back({128, 1, 0, 1});
     }
+    TuneChoice forced;
+    if (!h->ensemble && forced_launch(forced)) {
+        if (forced.pipe && !pipe_ok) forced.pipe = 0;
+        if (!fp32_math) forced.minb = 1;
+        h->block = forced.block;
+        h->minb = forced.minb;
+        h->grid = 0;
+        h->pipe = forced.pipe;
+        return FPCLBM_OK;
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        load_tune_file();
         auto it = g_tune_cache.find(tune_key(h));
         if (it != g_tune_cache.end()) {
             h->block = it->second.block;
@@ -352,6 +406,10 @@ int autotune(fpclbm* h)
     h->pipe = win.pipe;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[tune_key(h)] = win;
+    save_tune_file();
+    if (verbose())
+        std::fprintf(stderr, "fpclbm tune %s: chose block %d minb %d grid %d pipe %d\n", tune_key(h).c_str(),
+                     win.block, win.minb, win.grid, win.pipe);
     return FPCLBM_OK;
 }
 

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128, MINB) k_step_pipe(const StepArgs<R> a, un
             S* dst = sm + (size_t)stage * 27 * T + tid;
 #pragma unroll
             for (int s = 0; s < 27; ++s)
-                cp_async<sizeof(S)>(dst + s * T, buf + (size_t)load_off<ODD, WALLS>(s, n, stride, cell));
+                cp_async<sizeof(S)>(dst + s * T, load_ptr<S, ODD, WALLS>(buf, s, n, stride, cell));
         }
         cp_async_commit();
     };
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(128, MINB) k_step_pipe(const StepArgs<R> a, un
             Nbr n;
             if (ODD) n = make_nbr<WALLS>(G, cell);
 #pragma unroll
-            for (int s = 0; s < 27; ++s) Store<S>::st(buf + (size_t)store_off<ODD, WALLS>(s, n, stride, cell), g[s]);
+            for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, WALLS>(buf, s, n, stride, cell), g[s]);
         }
         stage ^= 1;
     }

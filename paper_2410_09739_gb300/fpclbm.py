@@ -47,7 +47,8 @@ PRECISIONS = {"fp64": FPCLBM_FP64, "fp32": FPCLBM_FP32, "fp16": FPCLBM_FP32_STOR
 EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fpclbm_set_params",
             "fpclbm_set_rates", "fpclbm_set_force", "fpclbm_step", "fpclbm_moments", "fpclbm_diagnostics",
             "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_set_closure",
-            "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc")
+            "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc", "fpclbm_closure_sample",
+            "fpclbm_closure_train", "fpclbm_closure_grad")
 
 
 class FpclbmError(RuntimeError):
@@ -87,6 +88,10 @@ def load(path: str = LIB_PATH):
     L.fpclbm_set_closure.argtypes = [_P, ctypes.POINTER(ctypes.c_ushort), ctypes.c_int]
     L.fpclbm_diagnostics_noalloc.argtypes = [_P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, _P, _P]
+    L.fpclbm_closure_sample.argtypes = [_P, ctypes.c_int, ctypes.c_double, _P, _P, ctypes.c_int]
+    L.fpclbm_closure_train.argtypes = [_P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ushort), _D, _P]
+    L.fpclbm_closure_grad.argtypes = [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_ushort), _P, _D, _P]
     L.fpclbm_destroy.argtypes = [_P]
     L.fpclbm_last_error.argtypes = [_P]
     L.fpclbm_last_error.restype = ctypes.c_char_p
@@ -211,6 +216,52 @@ def fpclbm_diagnostics_noalloc(f_dev, ncells: int, Fx: float, Fy: float, Fz: flo
     rc = load().fpclbm_diagnostics_noalloc(_ptr(f_dev, 1), int(ncells), float(Fx), float(Fy), float(Fz),
                                            _ptr(out_dev, 1), _P(stream) if stream else None)
     return _check(None, rc)
+
+
+def _fptr(a, on_device: bool):
+    """Pointer of a float32 array (numpy host array, or torch tensor on the matching device)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous() or a.is_cuda != bool(on_device):
+                raise TypeError("need a contiguous float32 tensor on the %s" % ("GPU" if on_device else "host"))
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:  # pragma: no cover
+        pass
+    if on_device:
+        raise TypeError("on_device=1 needs a CUDA torch tensor")
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("host arrays must be C-contiguous float32 numpy arrays")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def fpclbm_closure_sample(h, r: int, tau_coarse: float, X, T, on_device: int = 0):
+    """Features X [nc, 9] and labels T [nc] (float32) of the r^3-filtered fine box."""
+    return _check(h, load().fpclbm_closure_sample(h, int(r), float(tau_coarse), _fptr(X, on_device),
+                                                  _fptr(T, on_device), int(on_device)))
+
+
+def fpclbm_closure_train(X_dev, T_dev, n: int, epochs: int, batch: int, lr: float, seed: int = 0, stream: int = 0):
+    """Train on device tensors; returns (bf16 weight bits [4865] uint16, loss per epoch)."""
+    w = np.zeros(4865, dtype=np.uint16)
+    losses = np.zeros(int(epochs))
+    rc = load().fpclbm_closure_train(_fptr(X_dev, 1), _fptr(T_dev, 1), int(n), int(epochs), int(batch), float(lr),
+                                     int(seed), w.ctypes.data_as(ctypes.POINTER(ctypes.c_ushort)),
+                                     losses.ctypes.data_as(_D), _P(stream) if stream else None)
+    _check(None, rc)
+    return w, losses
+
+
+def fpclbm_closure_grad(X_dev, T_dev, n: int, bf16_bits, stream: int = 0):
+    """(loss, grad [4865] float32) of the network with the given bf16 weights on device samples."""
+    w = np.ascontiguousarray(np.asarray(bf16_bits, dtype=np.uint16))
+    g = np.zeros(4865, dtype=np.float32)
+    loss = ctypes.c_double()
+    rc = load().fpclbm_closure_grad(_fptr(X_dev, 1), _fptr(T_dev, 1), int(n),
+                                    w.ctypes.data_as(ctypes.POINTER(ctypes.c_ushort)), _fptr(g, 0),
+                                    ctypes.byref(loss), _P(stream) if stream else None)
+    _check(None, rc)
+    return loss.value, g
 
 
 def fpclbm_destroy(h):
