@@ -25,7 +25,9 @@
  *     grouping applied as a 27x27 matrix G and undone by its numerical
  *     inverse;
  *   - half-force velocity of Appendix D Step 7, push streaming of Step 6
- *     (Eq. LBMsteps), half-way bounce-back on y-walls (Sec. 4 cubic cavity).
+ *     (Eq. LBMsteps), half-way bounce-back on y-walls or on all six faces of
+ *     a closed box, with the moving-wall momentum correction on the wall
+ *     y = ny-1/2 (Sec. 4 cubic cavity).
  *
  * Readings where the paper is silent or self-contradictory (each one is
  * listed with its reason in the design notes of the repository):
@@ -39,7 +41,11 @@
  *       moments);
  *   R4  initial populations are f = C(u)^-1 kappa^eq(rho,u) with kappa^eq the
  *       MCM attractors (no non-equilibrium part);
- *   R5  sources of order >= 3 use the pre-collision central moments.
+ *   R5  sources of order >= 3 use the pre-collision central moments;
+ *   R6  moving wall: the density in the momentum correction is that of the
+ *       fluid cell the population leaves, and the moving wall is the whole
+ *       layer y = ny, so links through its edges and corners are corrected
+ *       too.
  *
  * Layout of population arrays: f[a][z][y][x], a = 0..26 (alpha-major), full
  * populations (not deviations), fp64.
@@ -406,49 +412,88 @@ int orc_init_equilibrium(int nx, int ny, int nz, const double* rho, const double
 }
 
 /* One time step: collision (Steps 7,1-5) then push streaming (Step 6).
- * bc = 0: periodic in x, y, z; bc = 1: half-way bounce-back walls at
- * y = -1/2 and y = ny-1/2, periodic in x and z. */
-int orc_step(int nx, int ny, int nz, int bc, const double* fin, double* fout,
-             const double F[3], const double omega[Q], int mode)
+ * bc = 0: periodic in x, y, z;
+ * bc = 1: half-way bounce-back walls at y = -1/2 and y = ny-1/2, periodic in
+ *         x and z (channel);
+ * bc = 2: closed box, half-way bounce-back walls at -1/2 and n-1/2 on all
+ *         three axes (the cubic cavity of Sec. 4).
+ * uw is the velocity of the wall at y = ny-1/2 (bc 1 and 2; it must be
+ * tangential, uw[1] = 0).  The population that leaves cell x along e_a
+ * towards a solid point is reflected into the opposite direction at x; when
+ * that point lies in the layer y = ny (every link with e_ay = +1 out of the
+ * top row, edges and corners included) it carries the moving-wall momentum
+ * correction of half-way bounce-back (Sec. 4 cubic cavity, "momentum
+ * correction to the moving wall"):
+ *   f_opp(a)(x, t+1) = ft_a(x, t) - 2 w_a rho(x, t) (e_a . uw) / cs^2,
+ * with w_a the rest weights (equilibrium at rho = 1, u = 0) and rho(x, t)
+ * the density of the fluid cell. */
+int orc_step_bc(int nx, int ny, int nz, int bc, const double* fin, double* fout,
+                const double F[3], const double omega[Q], int mode, const double uw[3])
 {
     const long N = (long)nx * ny * nz;
+    if (bc < 0 || bc > 2 || (bc == 0 && (uw[0] != 0 || uw[2] != 0)) || uw[1] != 0) return -2;
     int opp[Q];
     for (int a = 0; a < Q; ++a) opp[a] = opposite(a);
+    double w[Q];
+    const double zero[3] = {0, 0, 0};
+    if (orc_equilibrium(1.0, zero, w) != 0) return -1;
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 const long c = x + (long)nx * (y + (long)ny * z);
-                double f[Q], ft[Q];
-                for (int a = 0; a < Q; ++a) f[a] = fin[a * N + c];
+                double f[Q], ft[Q], rho = 0;
+                for (int a = 0; a < Q; ++a) {
+                    f[a] = fin[a * N + c];
+                    rho += f[a];
+                }
                 if (orc_collide(f, F, omega, mode, ft) != 0) bad |= 1;
                 for (int a = 0; a < Q; ++a) {
-                    const long yd = y + EY[a];
-                    if (bc == 1 && (yd < 0 || yd >= ny)) {
-                        fout[opp[a] * N + c] = ft[a]; /* half-way bounce-back */
+                    const long xd = x + EX[a], yd = y + EY[a], zd = z + EZ[a];
+                    const int out_y = bc >= 1 && (yd < 0 || yd >= ny);
+                    const int out_xz = bc == 2 && (xd < 0 || xd >= nx || zd < 0 || zd >= nz);
+                    if (out_y || out_xz) { /* half-way bounce-back */
+                        double v = ft[a];
+                        if (yd == ny) v -= 2.0 * w[a] * rho * (EX[a] * uw[0] + EZ[a] * uw[2]) / CS2;
+                        fout[opp[a] * N + c] = v;
                         continue;
                     }
-                    const long xd = wrap(x + EX[a], nx), zd = wrap(z + EZ[a], nz);
-                    const long yw = wrap(yd, ny);
-                    fout[a * N + xd + nx * (yw + (long)ny * zd)] = ft[a];
+                    const long xw = wrap(xd, nx), yw = wrap(yd, ny), zw = wrap(zd, nz);
+                    fout[a * N + xw + nx * (yw + (long)ny * zw)] = ft[a];
                 }
             }
     return bad ? -1 : 0;
 }
 
+/* orc_step_bc with resting walls. */
+int orc_step(int nx, int ny, int nz, int bc, const double* fin, double* fout,
+             const double F[3], const double omega[Q], int mode)
+{
+    const double still[3] = {0, 0, 0};
+    return orc_step_bc(nx, ny, nz, bc, fin, fout, F, omega, mode, still);
+}
+
 /* n time steps; f is updated in place, work is scratch of the same size. */
-int orc_run(int nx, int ny, int nz, int bc, double* f, double* work, const double F[3],
-            const double omega[Q], int mode, long nsteps)
+int orc_run_bc(int nx, int ny, int nz, int bc, double* f, double* work, const double F[3],
+               const double omega[Q], int mode, long nsteps, const double uw[3])
 {
     const long N = (long)nx * ny * nz;
     double *a = f, *b = work;
-    for (long t = 0; t < nsteps; ++t) {
-        if (orc_step(nx, ny, nz, bc, a, b, F, omega, mode) != 0) return -1;
+    int rc = 0;
+    for (long t = 0; t < nsteps && rc == 0; ++t) {
+        rc = orc_step_bc(nx, ny, nz, bc, a, b, F, omega, mode, uw);
         double* tmp = a; a = b; b = tmp;
     }
     if (a != f) memcpy(f, a, sizeof(double) * Q * N);
-    return 0;
+    return rc;
+}
+
+int orc_run(int nx, int ny, int nz, int bc, double* f, double* work, const double F[3],
+            const double omega[Q], int mode, long nsteps)
+{
+    const double still[3] = {0, 0, 0};
+    return orc_run_bc(nx, ny, nz, bc, f, work, F, omega, mode, nsteps, still);
 }
 
 /* Step 7: rho and u (with half force) of every cell. */

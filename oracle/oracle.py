@@ -20,6 +20,7 @@ __all__ = [
     "lib", "velocity_set", "moment_exponents", "central_matrix", "grouping_matrix",
     "attractor_generic", "maxwell_moments", "collide", "equilibrium", "init_equilibrium",
     "step", "run", "moments", "rates", "threads", "EQ_MODE_FP", "EQ_MODE_MCM",
+    "BC_PERIODIC", "BC_WALLS_Y", "BC_BOX",
 ]
 
 EQ_MODE_FP = 0   # diffusion tensor of Eq. (diffusion-tensor-parameter-3D)
@@ -47,10 +48,10 @@ def lib():
         L.orc_equilibrium.restype = ctypes.c_int
         L.orc_init_equilibrium.argtypes = [ctypes.c_int] * 3 + [_D] * 5
         L.orc_init_equilibrium.restype = ctypes.c_int
-        L.orc_step.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int]
-        L.orc_step.restype = ctypes.c_int
-        L.orc_run.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int, ctypes.c_long]
-        L.orc_run.restype = ctypes.c_int
+        L.orc_step_bc.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int, _D]
+        L.orc_step_bc.restype = ctypes.c_int
+        L.orc_run_bc.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int, ctypes.c_long, _D]
+        L.orc_run_bc.restype = ctypes.c_int
         L.orc_moments.argtypes = [ctypes.c_int] * 3 + [_D, _D, _D, _D, _D, _D]
         L.orc_rates.argtypes = [ctypes.c_double, ctypes.c_double, _D]
         L.orc_velocity_set.argtypes = [_I, _I, _I]
@@ -137,30 +138,39 @@ def init_equilibrium(rho, ux, uy, uz) -> np.ndarray:
     return f
 
 
-def step(f, bc: int = 0, F=(0.0, 0.0, 0.0), omega=None, mode: int = EQ_MODE_FP) -> np.ndarray:
-    """One time step (collide + stream); returns the new populations."""
+BC_PERIODIC, BC_WALLS_Y, BC_BOX = 0, 1, 2
+
+
+def _check(rc: int):
+    if rc == -2:
+        raise ValueError("bad boundary condition or wall velocity (bc in 0..2, tangential lid, no lid when periodic)")
+    if rc != 0:
+        raise FloatingPointError("singular central-moment matrix")
+
+
+def step(f, bc: int = 0, F=(0.0, 0.0, 0.0), omega=None, mode: int = EQ_MODE_FP, uw=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """One time step (collide + stream); returns the new populations.  bc: 0 periodic, 1 walls at
+    y = -1/2, ny - 1/2, 2 closed box; uw: velocity of the wall at y = ny - 1/2."""
     f = _arr(f)
     _, nz, ny, nx = f.shape
     out = np.zeros_like(f)
     if omega is None:
         omega = np.ones(27)
-    rc = lib().orc_step(nx, ny, nz, int(bc), _p(f), _p(out), _p(_arr(F, 3)), _p(_arr(omega, 27)), int(mode))
-    if rc != 0:
-        raise FloatingPointError("singular central-moment matrix")
+    _check(lib().orc_step_bc(nx, ny, nz, int(bc), _p(f), _p(out), _p(_arr(F, 3)), _p(_arr(omega, 27)), int(mode),
+                             _p(_arr(uw, 3))))
     return out
 
 
-def run(f, nsteps: int, bc: int = 0, F=(0.0, 0.0, 0.0), omega=None, mode: int = EQ_MODE_FP) -> np.ndarray:
+def run(f, nsteps: int, bc: int = 0, F=(0.0, 0.0, 0.0), omega=None, mode: int = EQ_MODE_FP,
+        uw=(0.0, 0.0, 0.0)) -> np.ndarray:
     """``nsteps`` time steps; returns the new populations (input untouched)."""
     f = _arr(f).copy()
     _, nz, ny, nx = f.shape
     work = np.zeros_like(f)
     if omega is None:
         omega = np.ones(27)
-    rc = lib().orc_run(nx, ny, nz, int(bc), _p(f), _p(work), _p(_arr(F, 3)), _p(_arr(omega, 27)),
-                       int(mode), int(nsteps))
-    if rc != 0:
-        raise FloatingPointError("singular central-moment matrix")
+    _check(lib().orc_run_bc(nx, ny, nz, int(bc), _p(f), _p(work), _p(_arr(F, 3)), _p(_arr(omega, 27)),
+                            int(mode), int(nsteps), _p(_arr(uw, 3))))
     return f
 
 
