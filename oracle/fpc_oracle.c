@@ -27,7 +27,10 @@
  *   - half-force velocity of Appendix D Step 7, push streaming of Step 6
  *     (Eq. LBMsteps), half-way bounce-back on y-walls or on all six faces of
  *     a closed box, with the moving-wall momentum correction on the wall
- *     y = ny-1/2 (Sec. 4 cubic cavity).
+ *     y = ny-1/2 (Sec. 4 cubic cavity), or a half channel closed by a
+ *     specular-reflection symmetry plane (Sec. 4 turbulent channel);
+ *   - the Smagorinsky subgrid model with van Driest wall damping (Sec. 4
+ *     turbulent channel LES).
  *
  * Readings where the paper is silent or self-contradictory (each one is
  * listed with its reason in the design notes of the repository):
@@ -45,7 +48,13 @@
  *   R6  moving wall: the density in the momentum correction is that of the
  *       fluid cell the population leaves, and the moving wall is the whole
  *       layer y = ny, so links through its edges and corners are corrected
- *       too.
+ *       too;
+ *   R7  Smagorinsky model: the strain rate comes from the deviatoric part of
+ *       the non-equilibrium second-order central moments, the force's
+ *       contribution to them is neglected, Delta = 1, and the eddy viscosity
+ *       replaces all five shear rates; van Driest damping uses the distance
+ *       of the cell centre to the nearest wall and the nominal friction
+ *       velocity u*.
  *
  * Layout of population arrays: f[a][z][y][x], a = 0..26 (alpha-major), full
  * populations (not deviations), fp64.
@@ -411,32 +420,110 @@ int orc_init_equilibrium(int nx, int ny, int nz, const double* rho, const double
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Smagorinsky subgrid model with van Driest damping (Sec. 4, turbulent     */
+/* channel; the paper names the model and cites it, the formulas below are   */
+/* the standard definitions, reading R7)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Effective shear relaxation time of one cell:
+ *   nu_t = c2 |S|,  |S| = sqrt(2 S_ij S_ij),  c2 = (C_s Delta D)^2, Delta = 1,
+ *   S_ij = -Pi^d_ij / (2 rho cs^2 tau),  tau = tau0 + nu_t / cs^2,
+ * with Pi_ij = kappa_ij - cs^2 rho delta_ij the non-equilibrium second-order
+ * central moments of the incoming populations (at the half-force velocity)
+ * and Pi^d its deviatoric part (the trace belongs to the bulk rate, which the
+ * model leaves alone).  tau is the root of the defining relation, found by
+ * bisection. */
+double orc_smagorinsky_tau(const double f[Q], const double F[3], double tau0, double c2)
+{
+    double rho = 0, j[3] = {0, 0, 0};
+    for (int a = 0; a < Q; ++a) {
+        rho += f[a];
+        j[0] += f[a] * EX[a];
+        j[1] += f[a] * EY[a];
+        j[2] += f[a] * EZ[a];
+    }
+    const double u[3] = {(j[0] + 0.5 * F[0]) / rho, (j[1] + 0.5 * F[1]) / rho, (j[2] + 0.5 * F[2]) / rho};
+    double P[3][3] = {{0}};
+    for (int a = 0; a < Q; ++a) {
+        const double c[3] = {EX[a] - u[0], EY[a] - u[1], EZ[a] - u[2]};
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) P[i][k] += f[a] * c[i] * c[k];
+    }
+    for (int i = 0; i < 3; ++i) P[i][i] -= CS2 * rho;
+    const double tr = (P[0][0] + P[1][1] + P[2][2]) / 3.0;
+    for (int i = 0; i < 3; ++i) P[i][i] -= tr;
+    double pp = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) pp += P[i][k] * P[i][k];
+    const double Pn = sqrt(2.0 * pp); /* |Pi^d| = sqrt(2 Pi^d : Pi^d) */
+    /* g(tau) = tau - tau0 - c2 |S(tau)| / cs^2 is increasing on tau >= tau0 */
+    double lo = tau0, hi = tau0 + c2 * Pn / (2.0 * rho * CS2 * tau0) / CS2;
+    for (int it = 0; it < 200 && hi > lo; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double g = mid - tau0 - c2 * (Pn / (2.0 * rho * CS2 * mid)) / CS2;
+        if (g > 0) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Distance of cell row y (cell centre) to the nearest wall of boundary kind
+ * bc along y, or a negative value when there is none (bc 0; bc 2 uses all
+ * three axes and is handled by the caller). */
+static double wall_distance_y(int bc, int y, int ny)
+{
+    if (bc == 1) { const double a = y + 0.5, b = ny - 0.5 - y; return a < b ? a : b; }
+    if (bc == 3) return y + 0.5;
+    return -1.0;
+}
+
+/* van Driest damping D = 1 - exp(-y+ / A+), y+ = y_w u* / nu. */
+static double van_driest(double yw, double u_star, double nu, double a_plus)
+{
+    if (yw < 0 || u_star <= 0 || a_plus <= 0) return 1.0;
+    return 1.0 - exp(-(yw * u_star / nu) / a_plus);
+}
+
 /* One time step: collision (Steps 7,1-5) then push streaming (Step 6).
  * bc = 0: periodic in x, y, z;
  * bc = 1: half-way bounce-back walls at y = -1/2 and y = ny-1/2, periodic in
  *         x and z (channel);
  * bc = 2: closed box, half-way bounce-back walls at -1/2 and n-1/2 on all
- *         three axes (the cubic cavity of Sec. 4).
+ *         three axes (the cubic cavity of Sec. 4);
+ * bc = 3: half channel (Sec. 4, turbulent channel): bounce-back wall at
+ *         y = -1/2 and a specular-reflection symmetry plane at y = ny-1/2: a
+ *         population leaving the top row along (ex, +1, ez) comes back along
+ *         (ex, -1, ez) into the top row, shifted by (ex, ez) in x and z.
  * uw is the velocity of the wall at y = ny-1/2 (bc 1 and 2; it must be
  * tangential, uw[1] = 0).  The population that leaves cell x along e_a
  * towards a solid point is reflected into the opposite direction at x; when
  * that point lies in the layer y = ny (every link with e_ay = +1 out of the
  * top row, edges and corners included) it carries the moving-wall momentum
- * correction of half-way bounce-back (Sec. 4 cubic cavity, "momentum
- * correction to the moving wall"):
+ * correction of half-way bounce-back that Sec. 4 applies to the cavity lid
+ * (Ladd's form):
  *   f_opp(a)(x, t+1) = ft_a(x, t) - 2 w_a rho(x, t) (e_a . uw) / cs^2,
  * with w_a the rest weights (equilibrium at rho = 1, u = 0) and rho(x, t)
- * the density of the fluid cell. */
-int orc_step_bc(int nx, int ny, int nz, int bc, const double* fin, double* fout,
-                const double F[3], const double omega[Q], int mode, const double uw[3])
+ * the density of the fluid cell.
+ * les (optional, NULL for none) = {C_s, u*, A+}: Smagorinsky model with van
+ * Driest damping; every cell's shear rates omega_4,5,6,8,9 become
+ * 1 / orc_smagorinsky_tau(f, F, 1/omega_4, (C_s D)^2). */
+int orc_step_les(int nx, int ny, int nz, int bc, const double* fin, double* fout,
+                 const double F[3], const double omega[Q], int mode, const double uw[3],
+                 const double* les)
 {
     const long N = (long)nx * ny * nz;
-    if (bc < 0 || bc > 2 || (bc == 0 && (uw[0] != 0 || uw[2] != 0)) || uw[1] != 0) return -2;
-    int opp[Q];
-    for (int a = 0; a < Q; ++a) opp[a] = opposite(a);
+    if (bc < 0 || bc > 3 || ((bc == 0 || bc == 3) && (uw[0] != 0 || uw[2] != 0)) || uw[1] != 0) return -2;
+    int opp[Q], mir[Q];
+    for (int a = 0; a < Q; ++a) {
+        opp[a] = opposite(a);
+        for (int b = 0; b < Q; ++b)
+            if (EX[b] == EX[a] && EY[b] == -EY[a] && EZ[b] == EZ[a]) mir[a] = b;
+    }
     double w[Q];
     const double zero[3] = {0, 0, 0};
     if (orc_equilibrium(1.0, zero, w) != 0) return -1;
+    const double tau0 = 1.0 / omega[4], nu0 = CS2 * (tau0 - 0.5);
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (int z = 0; z < nz; ++z)
@@ -448,9 +535,29 @@ int orc_step_bc(int nx, int ny, int nz, int bc, const double* fin, double* fout,
                     f[a] = fin[a * N + c];
                     rho += f[a];
                 }
-                if (orc_collide(f, F, omega, mode, ft) != 0) bad |= 1;
+                const double* om = omega;
+                double om_les[Q];
+                if (les) {
+                    double yw = wall_distance_y(bc, y, ny);
+                    if (bc == 2) {
+                        const double d[6] = {x + 0.5, nx - 0.5 - x, y + 0.5, ny - 0.5 - y, z + 0.5, nz - 0.5 - z};
+                        yw = d[0];
+                        for (int k = 1; k < 6; ++k) if (d[k] < yw) yw = d[k];
+                    }
+                    const double cd = les[0] * van_driest(yw, les[1], nu0, les[2]);
+                    const double te = orc_smagorinsky_tau(f, F, tau0, cd * cd);
+                    memcpy(om_les, omega, sizeof(om_les));
+                    om_les[4] = om_les[5] = om_les[6] = om_les[8] = om_les[9] = 1.0 / te;
+                    om = om_les;
+                }
+                if (orc_collide(f, F, om, mode, ft) != 0) bad |= 1;
                 for (int a = 0; a < Q; ++a) {
                     const long xd = x + EX[a], yd = y + EY[a], zd = z + EZ[a];
+                    if (bc == 3 && yd >= ny) { /* specular reflection at the symmetry plane */
+                        const long xw = wrap(xd, nx), zw = wrap(zd, nz);
+                        fout[mir[a] * N + xw + nx * ((long)(ny - 1) + (long)ny * zw)] = ft[a];
+                        continue;
+                    }
                     const int out_y = bc >= 1 && (yd < 0 || yd >= ny);
                     const int out_xz = bc == 2 && (xd < 0 || xd >= nx || zd < 0 || zd >= nz);
                     if (out_y || out_xz) { /* half-way bounce-back */
@@ -466,6 +573,12 @@ int orc_step_bc(int nx, int ny, int nz, int bc, const double* fin, double* fout,
     return bad ? -1 : 0;
 }
 
+int orc_step_bc(int nx, int ny, int nz, int bc, const double* fin, double* fout,
+                const double F[3], const double omega[Q], int mode, const double uw[3])
+{
+    return orc_step_les(nx, ny, nz, bc, fin, fout, F, omega, mode, uw, NULL);
+}
+
 /* orc_step_bc with resting walls. */
 int orc_step(int nx, int ny, int nz, int bc, const double* fin, double* fout,
              const double F[3], const double omega[Q], int mode)
@@ -475,18 +588,24 @@ int orc_step(int nx, int ny, int nz, int bc, const double* fin, double* fout,
 }
 
 /* n time steps; f is updated in place, work is scratch of the same size. */
-int orc_run_bc(int nx, int ny, int nz, int bc, double* f, double* work, const double F[3],
-               const double omega[Q], int mode, long nsteps, const double uw[3])
+int orc_run_les(int nx, int ny, int nz, int bc, double* f, double* work, const double F[3],
+                const double omega[Q], int mode, long nsteps, const double uw[3], const double* les)
 {
     const long N = (long)nx * ny * nz;
     double *a = f, *b = work;
     int rc = 0;
     for (long t = 0; t < nsteps && rc == 0; ++t) {
-        rc = orc_step_bc(nx, ny, nz, bc, a, b, F, omega, mode, uw);
+        rc = orc_step_les(nx, ny, nz, bc, a, b, F, omega, mode, uw, les);
         double* tmp = a; a = b; b = tmp;
     }
     if (a != f) memcpy(f, a, sizeof(double) * Q * N);
     return rc;
+}
+
+int orc_run_bc(int nx, int ny, int nz, int bc, double* f, double* work, const double F[3],
+               const double omega[Q], int mode, long nsteps, const double uw[3])
+{
+    return orc_run_les(nx, ny, nz, bc, f, work, F, omega, mode, nsteps, uw, NULL);
 }
 
 int orc_run(int nx, int ny, int nz, int bc, double* f, double* work, const double F[3],

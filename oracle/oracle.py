@@ -20,7 +20,7 @@ __all__ = [
     "lib", "velocity_set", "moment_exponents", "central_matrix", "grouping_matrix",
     "attractor_generic", "maxwell_moments", "collide", "equilibrium", "init_equilibrium",
     "step", "run", "moments", "rates", "threads", "EQ_MODE_FP", "EQ_MODE_MCM",
-    "BC_PERIODIC", "BC_WALLS_Y", "BC_BOX",
+    "BC_PERIODIC", "BC_WALLS_Y", "BC_BOX", "BC_HALF_CHANNEL", "smagorinsky_tau",
 ]
 
 EQ_MODE_FP = 0   # diffusion tensor of Eq. (diffusion-tensor-parameter-3D)
@@ -48,10 +48,12 @@ def lib():
         L.orc_equilibrium.restype = ctypes.c_int
         L.orc_init_equilibrium.argtypes = [ctypes.c_int] * 3 + [_D] * 5
         L.orc_init_equilibrium.restype = ctypes.c_int
-        L.orc_step_bc.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int, _D]
-        L.orc_step_bc.restype = ctypes.c_int
-        L.orc_run_bc.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int, ctypes.c_long, _D]
-        L.orc_run_bc.restype = ctypes.c_int
+        L.orc_step_les.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int, _D, _D]
+        L.orc_step_les.restype = ctypes.c_int
+        L.orc_run_les.argtypes = [ctypes.c_int] * 4 + [_D, _D, _D, _D, ctypes.c_int, ctypes.c_long, _D, _D]
+        L.orc_run_les.restype = ctypes.c_int
+        L.orc_smagorinsky_tau.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double]
+        L.orc_smagorinsky_tau.restype = ctypes.c_double
         L.orc_moments.argtypes = [ctypes.c_int] * 3 + [_D, _D, _D, _D, _D, _D]
         L.orc_rates.argtypes = [ctypes.c_double, ctypes.c_double, _D]
         L.orc_velocity_set.argtypes = [_I, _I, _I]
@@ -138,40 +140,53 @@ def init_equilibrium(rho, ux, uy, uz) -> np.ndarray:
     return f
 
 
-BC_PERIODIC, BC_WALLS_Y, BC_BOX = 0, 1, 2
+BC_PERIODIC, BC_WALLS_Y, BC_BOX, BC_HALF_CHANNEL = 0, 1, 2, 3
 
 
 def _check(rc: int):
     if rc == -2:
-        raise ValueError("bad boundary condition or wall velocity (bc in 0..2, tangential lid, no lid when periodic)")
+        raise ValueError("bad boundary condition or wall velocity (bc in 0..3, tangential lid, no lid when periodic "
+                         "or half channel)")
     if rc != 0:
         raise FloatingPointError("singular central-moment matrix")
 
 
-def step(f, bc: int = 0, F=(0.0, 0.0, 0.0), omega=None, mode: int = EQ_MODE_FP, uw=(0.0, 0.0, 0.0)) -> np.ndarray:
+def _les(les):
+    return None if les is None else _p(_arr(les, 3))
+
+
+def step(f, bc: int = 0, F=(0.0, 0.0, 0.0), omega=None, mode: int = EQ_MODE_FP, uw=(0.0, 0.0, 0.0),
+         les=None) -> np.ndarray:
     """One time step (collide + stream); returns the new populations.  bc: 0 periodic, 1 walls at
-    y = -1/2, ny - 1/2, 2 closed box; uw: velocity of the wall at y = ny - 1/2."""
+    y = -1/2, ny - 1/2, 2 closed box, 3 half channel (wall at y = -1/2, symmetry plane at ny - 1/2);
+    uw: velocity of the wall at y = ny - 1/2; les: (C_s, u*, A+) for the Smagorinsky model with
+    van Driest damping, or None."""
     f = _arr(f)
     _, nz, ny, nx = f.shape
     out = np.zeros_like(f)
     if omega is None:
         omega = np.ones(27)
-    _check(lib().orc_step_bc(nx, ny, nz, int(bc), _p(f), _p(out), _p(_arr(F, 3)), _p(_arr(omega, 27)), int(mode),
-                             _p(_arr(uw, 3))))
+    _check(lib().orc_step_les(nx, ny, nz, int(bc), _p(f), _p(out), _p(_arr(F, 3)), _p(_arr(omega, 27)), int(mode),
+                              _p(_arr(uw, 3)), _les(les)))
     return out
 
 
 def run(f, nsteps: int, bc: int = 0, F=(0.0, 0.0, 0.0), omega=None, mode: int = EQ_MODE_FP,
-        uw=(0.0, 0.0, 0.0)) -> np.ndarray:
+        uw=(0.0, 0.0, 0.0), les=None) -> np.ndarray:
     """``nsteps`` time steps; returns the new populations (input untouched)."""
     f = _arr(f).copy()
     _, nz, ny, nx = f.shape
     work = np.zeros_like(f)
     if omega is None:
         omega = np.ones(27)
-    _check(lib().orc_run_bc(nx, ny, nz, int(bc), _p(f), _p(work), _p(_arr(F, 3)), _p(_arr(omega, 27)),
-                            int(mode), int(nsteps), _p(_arr(uw, 3))))
+    _check(lib().orc_run_les(nx, ny, nz, int(bc), _p(f), _p(work), _p(_arr(F, 3)), _p(_arr(omega, 27)),
+                             int(mode), int(nsteps), _p(_arr(uw, 3)), _les(les)))
     return f
+
+
+def smagorinsky_tau(f, F=(0.0, 0.0, 0.0), tau0: float = 0.6, c2: float = 0.0) -> float:
+    """Effective shear relaxation time of one cell under the Smagorinsky model, c2 = (C_s Delta D)^2."""
+    return float(lib().orc_smagorinsky_tau(_p(_arr(f, 27)), _p(_arr(F, 3)), float(tau0), float(c2)))
 
 
 def moments(f, F=(0.0, 0.0, 0.0)):

@@ -128,4 +128,6 @@ def test_bad_boundary_arguments_are_rejected():
     with pytest.raises(ValueError):
         O.step(f0, bc=O.BC_PERIODIC, uw=(0.01, 0, 0))  # no wall to move
     with pytest.raises(ValueError):
-        O.step(f0, bc=3)
+        O.step(f0, bc=4)
+    with pytest.raises(ValueError):
+        O.step(f0, bc=O.BC_HALF_CHANNEL, uw=(0.01, 0, 0))  # a symmetry plane does not move
