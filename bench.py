@@ -49,12 +49,12 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--size", type=int, default=256, help="TGV box side")
     p.add_argument("--precision", default="fp32", choices=list(BYTES))
     p.add_argument("--inner", type=int, default=64, help="LBM steps per bench step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variants", action="store_true", help="also time fp16/bf16 storage")
-    p.add_argument("--workload", default="tgv", choices=["tgv", "channel", "ensemble"])
+    p.add_argument("--workload", default="tgv", choices=["tgv", "channel", "cavity", "ensemble"])
     return p.parse_args()
 
 
@@ -62,11 +62,12 @@ def dist_init(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 and args.impl == "ours":
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        dist.init_process_group("nccl")
+    # the reference arm (CPU oracle) runs on rank 0 alone; other ranks exit without work
     return rank, world, local
 
 
@@ -81,7 +82,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -199,7 +201,7 @@ def cpu_oracle_sample(n, tau, u0, target_s=15.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    n, u0 = args.n, 0.05
+    n, u0 = args.size, 0.05
     tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
     import oracle as O
     rho, ux, uy, uz = W.tgv(n, u0)
@@ -244,7 +246,7 @@ def time_ours(lat, F, torch, args, n, steps, warmup, inner):
 def setup(args, F, prec, stream):
     """Build the lattice of the chosen workload; returns (lat, flat fields, cells, config dict)."""
     if args.workload == "tgv":
-        n, u0 = args.n, 0.05
+        n, u0 = args.size, 0.05
         tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
         lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_PERIODIC, stream=stream)
         lat.set_params(tau)
@@ -259,6 +261,15 @@ def setup(args, F, prec, stream):
         lat.set_force(u_star ** 2 / H, 0.0, 0.0)
         flds = W.channel_fields(nx, ny, nz, u_star, seed=7)
         cfg = {"workload": "channel Re_tau=180 384x192x192, y walls, body force, tau=%.6f" % tau}
+    elif args.workload == "cavity":
+        n, U0 = 150, 0.1 / 3 ** 0.5
+        tau = 0.5 + 3 * U0 * n / 1000.0
+        lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_BOX, stream=stream)
+        lat.set_params(tau)
+        lat.set_wall_velocity(U0)
+        one = np.ones((n, n, n))
+        flds = (one, 0 * one, 0 * one, 0 * one)
+        cfg = {"workload": "lid-driven cubic cavity 150^3, Re=1000, Ma=0.1, walls on all faces, tau=%.6f" % tau}
     else:
         sides, taus = W.ensemble_config(256, seed=2410)
         dims = [(s_, s_, s_) for s_ in sides]
@@ -339,7 +350,7 @@ def main():
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": ncu_traffic(prec, args.n) if args.workload == "tgv" else None,
+                     "traffic": ncu_traffic(prec, args.size) if args.workload == "tgv" else None,
                      "peak_source": peak_kind, "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": ncell * args.inner * args.steps * world / results[prec]["e2e_s"] / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": 4 * 8 * ncell, "d2h_bytes_per_step": 4 * 8 * ncell},
@@ -351,7 +362,7 @@ def main():
                                "frac_hbm": 54 * BYTES[p] * ncell / (r["seconds"] / launches) / 1e9 / peak}
                            for p, r in results.items()}
     if world == 1 and not args.no_cpu_baseline:
-        n, u0 = args.n, 0.05
+        n, u0 = args.size, 0.05
         out["cpu_baseline"] = cpu_oracle_sample(n, 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5, u0)
     print(json.dumps(out), flush=True)
 

@@ -62,10 +62,17 @@ enum {
  * round-to-nearest-even. */
 enum { FPCLBM_FP64 = 0, FPCLBM_FP32 = 1, FPCLBM_FP32_STORE_FP16 = 2, FPCLBM_FP32_STORE_BF16 = 3 };
 
-/* Boundaries.  PERIODIC: periodic in x, y, z.  WALLS_Y: stationary half-way
- * bounce-back walls at y = -1/2 and y = ny - 1/2 (Sec. 4, cubic cavity),
- * periodic in x and z. */
-enum { FPCLBM_BC_PERIODIC = 0, FPCLBM_BC_WALLS_Y = 1 };
+/* Boundaries.  PERIODIC: periodic in x, y, z.  WALLS_Y: half-way bounce-back
+ * walls at y = -1/2 and y = ny - 1/2 (Sec. 4, cubic cavity), periodic in x
+ * and z (channel).  BOX: closed box, half-way bounce-back walls at -1/2 and
+ * n - 1/2 on all three axes (the cubic cavity of Sec. 4).  In WALLS_Y and BOX
+ * the wall y = ny - 1/2 may move tangentially (fpclbm_set_wall_velocity);
+ * every other wall rests.  HALF_CHANNEL: bounce-back wall at y = -1/2 and a
+ * specular-reflection symmetry plane at y = ny - 1/2, periodic in x and z
+ * (the half channel of the turbulent-channel LES, Sec. 4): a population that
+ * leaves the top row along (ex, +1, ez) re-enters it along (ex, -1, ez) at
+ * x + (ex, 0, ez). */
+enum { FPCLBM_BC_PERIODIC = 0, FPCLBM_BC_WALLS_Y = 1, FPCLBM_BC_BOX = 2, FPCLBM_BC_HALF_CHANNEL = 3 };
 
 /* Choice of the diffusion tensor D' inside the attractors.
  * FP: Eq. (diffusion-tensor-parameter-3D): D' = cs^2 delta for order <= 2 and
@@ -74,10 +81,14 @@ enum { FPCLBM_BC_PERIODIC = 0, FPCLBM_BC_WALLS_Y = 1 };
  *     their own attractors, i.e. Maxwellian central moments (the MCM-LBM the
  *     paper compares with, Sec. 4).
  * FP_LEARNED: FP plus the learned correction of the shear rates installed by
- *     fpclbm_set_closure (no counterpart in the paper). */
-enum { FPCLBM_DIFF_FP = 0, FPCLBM_DIFF_EQUILIBRIUM = 1, FPCLBM_DIFF_FP_LEARNED = 2 };
+ *     fpclbm_set_closure (no counterpart in the paper); periodic boxes and
+ *     channels with resting walls.
+ * FP_SMAGORINSKY: FP with the Smagorinsky eddy viscosity and van Driest wall
+ *     damping of the turbulent-channel LES (Sec. 4) in the five shear rates,
+ *     parameters from fpclbm_set_smagorinsky; boxes with resting walls. */
+enum { FPCLBM_DIFF_FP = 0, FPCLBM_DIFF_EQUILIBRIUM = 1, FPCLBM_DIFF_FP_LEARNED = 2, FPCLBM_DIFF_FP_SMAGORINSKY = 3 };
 
-/* Create a single periodic or channel box of nx*ny*nz cells (each >= 1,
+/* Create a single periodic, channel or closed box of nx*ny*nz cells (each >= 1,
  * product < 2^31).  cuda_stream is a cudaStream_t (NULL allowed).
  * Parameters start at tau = 1, drift = 0, diffusion = FP, F = 0; the
  * populations are undefined until fpclbm_init_fields/set_populations.
@@ -121,6 +132,31 @@ FPCLBM_API int fpclbm_set_rates(fpclbm_t h, const double omega[27]);
  * Eq. (forcing:3D); enters as sources sigma_mnp and the half-force velocity
  * of Step 7.  Errors: ARG (non-finite). */
 FPCLBM_API int fpclbm_set_force(fpclbm_t h, double Fx, double Fy, double Fz);
+
+/* Smagorinsky subgrid model for FPCLBM_DIFF_FP_SMAGORINSKY (Sec. 4, turbulent
+ * channel; the paper names the model, these are its standard definitions):
+ * per cell nu_t = (C_s D)^2 |S| (filter width 1), |S| = sqrt(2 S_ij S_ij) with
+ * the strain rate from the deviatoric non-equilibrium second-order central
+ * moments Pi^d of the incoming populations, S = -Pi^d / (2 rho cs^2 tau), at
+ * the effective time tau = tau0 + nu_t / cs^2 (tau0 = 1 / omega_4 of
+ * fpclbm_set_params); the closed-form root
+ * tau = (tau0 + sqrt(tau0^2 + 18 (C_s D)^2 |Pi^d| / rho)) / 2 sets all five
+ * shear rates to 1 / tau.  van Driest damping D = 1 - exp(-y+ / A+),
+ * y+ = y_w u* / nu0, y_w the distance of the cell centre to the nearest wall
+ * (WALLS_Y: both walls; HALF_CHANNEL: the wall at y = -1/2; PERIODIC: none,
+ * D = 1); u* <= 0 or A+ <= 0 switch the damping off.  Defaults 0, 0, 0.
+ * Errors: ARG (ensemble, C_s < 0, non-finite). */
+FPCLBM_API int fpclbm_set_smagorinsky(fpclbm_t h, double cs, double u_star, double a_plus);
+
+/* Tangential velocity (ux, 0, uz) of the wall y = ny - 1/2 of a WALLS_Y or
+ * BOX box (the lid of the lid-driven cavity, Sec. 4; the moving plate of
+ * Couette flow).  Half-way bounce-back with the moving-wall momentum
+ * correction: a population reflected through that wall is stored as
+ * f~_a - 2 w_a rho (e_a . u_w) / cs^2, with w_a the rest weights and rho the
+ * density of the fluid cell it leaves; links through the edges and corners of
+ * the wall's layer y = ny are corrected too.  Mass is conserved exactly.
+ * Starts at 0.  Errors: ARG (periodic box, ensemble, non-finite value). */
+FPCLBM_API int fpclbm_set_wall_velocity(fpclbm_t h, double ux, double uz);
 
 /* Advance n >= 0 time steps (collide + stream each).  Replays a captured CUDA
  * graph of the step loop; synchronises the stream once at the end and reads
@@ -245,6 +281,60 @@ FPCLBM_API int fpclbm_destroy(fpclbm_t h);
  * and valid until its next call.  With h = NULL: the last error of a failed
  * fpclbm_create / fpclbm_create_ensemble on this thread. */
 FPCLBM_API const char* fpclbm_last_error(fpclbm_t h);
+
+/* ------------------------------------------------------------------------ */
+/* The 2D FPC-LBM on the D2Q9 lattice (Sec. 2 and the appendix on the 2D     */
+/* algorithm).  A separate handle: periodic nx x ny boxes, populations in the */
+/* velocity order of Sec. 2 (e_x = 0,1,0,-1,0,1,-1,-1,1; e_y = 0,0,1,0,-1,1, */
+/* 1,-1,-1), stored as deviations from the rest weights (4/9, 1/9, 1/36) in  */
+/* the given precision, AA-pattern update in place.  Rates omega_0..omega_8  */
+/* in the 2D Step 3 numbering: 3 = 2s (bulk, zeta = cs^2 (1/omega_3 - 1/2)), */
+/* 4 = 2d and 5 = 11 (shear, nu = cs^2 (1/omega_4 - 1/2)), 6 = 21, 7 = 12,   */
+/* 8 = 22 (Eq. transportcoeff2DFPCLBM).  Return codes as above.              */
+/* ------------------------------------------------------------------------ */
+typedef struct fpclbm2d* fpclbm2d_t;
+
+/* Periodic nx x ny box (nx, ny >= 1, nx * ny < 2^31), any FPCLBM_* precision.
+ * Starts at tau = 1, unit rates, no force, FP mode.  Errors: ARG, ALLOC. */
+FPCLBM_API int fpclbm2d_create(fpclbm2d_t* out, int nx, int ny, int precision, void* cuda_stream);
+
+/* Equilibrium of (rho, ux, uy) per cell (x fastest), f = C(u)^-1 kappa^eq with
+ * the Maxwellian central moments; resets the step count.  on_device: the
+ * three arrays are device pointers.  Errors: ARG, CUDA. */
+FPCLBM_API int fpclbm2d_init_fields(fpclbm2d_t h, const double* rho, const double* ux, const double* uy,
+                                    int on_device);
+
+/* omega_4 = omega_5 = 1/tau; omega_3 = bulk_rate (0 selects 1); orders 3 and 4:
+ * order * drift when drift > 0, else 1 (as in 3D); diffusion: FPCLBM_DIFF_FP or
+ * FPCLBM_DIFF_EQUILIBRIUM (MCM).  Rates 3..8 must lie in (0, 2), else PARAM.
+ * Errors: ARG, PARAM. */
+FPCLBM_API int fpclbm2d_set_params(fpclbm2d_t h, double tau, double bulk_rate, double drift, int diffusion);
+
+/* Full override of omega_0..omega_8 (0..2 have no effect).  Errors: ARG, PARAM. */
+FPCLBM_API int fpclbm2d_set_rates(fpclbm2d_t h, const double omega[9]);
+
+/* Body force (Eq. forcing:2D).  Errors: ARG. */
+FPCLBM_API int fpclbm2d_set_force(fpclbm2d_t h, double Fx, double Fy);
+
+/* Advance n >= 0 steps; DIVERGED if a cell saw rho <= 0 or a non-finite value.
+ * Errors: ARG, STATE, CUDA, DIVERGED. */
+FPCLBM_API int fpclbm2d_step(fpclbm2d_t h, long long n);
+
+/* rho and the half-force velocity per cell (any pointer may be NULL).
+ * Errors: ARG, STATE, CUDA. */
+FPCLBM_API int fpclbm2d_moments(fpclbm2d_t h, double* rho, double* ux, double* uy, int on_device);
+
+/* Full populations f[alpha * N + cell] (host, 9 N doubles), in and out;
+ * setting them resets the step count.  Errors: ARG, STATE, CUDA. */
+FPCLBM_API int fpclbm2d_get_populations(fpclbm2d_t h, double* f);
+FPCLBM_API int fpclbm2d_set_populations(fpclbm2d_t h, const double* f);
+
+/* NULL-safe. */
+FPCLBM_API int fpclbm2d_destroy(fpclbm2d_t h);
+
+/* Message of the last failed call on h (or of the last failed create when h
+ * is NULL); owned by the library, valid until the next call. */
+FPCLBM_API const char* fpclbm2d_last_error(fpclbm2d_t h);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,152 @@
+"""Turbulent half-channel LES (Sec. 4): FPC-LBM with the Smagorinsky model and van Driest damping
+on a half channel closed by a specular symmetry plane, driven by F_x = u*^2 / H.
+
+Domain 2 pi H x H x pi H (x, y wall-normal, z), wall at y = -1/2, symmetry plane at y = H - 1/2,
+Re* = u* H / nu.  Initial state: the lower half of a laminar channel of height 2H with bulk
+velocity 16 u* plus seeded +-10 % perturbations.  After --spinup friction times T* = H / u*,
+statistics over --collect T* (every --every steps; averages over x, z and time):
+mean U(y), rms fluctuations, Reynolds shear stress -<u'v'>, all in wall units with the nominal u*.
+
+The paper compares with DNS data that are not reproduced here; the mean profile is set beside the
+textbook law of the wall instead: u+ = y+ in the viscous sublayer (y+ < 5) and
+u+ = ln(y+) / 0.41 + 5.2 in the log layer (30 < y+ < 0.3 Re*), and the total shear stress is
+checked against its exact linear profile u*^2 (1 - y/H) (momentum balance of the statistically
+steady channel: viscous + resolved Reynolds + subgrid stress).
+
+Usage: python -m paper_2410_09739_gb300.channel_les_study [--H 64] [--re-tau 180] ...
+Prints one JSON object.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+import workloads as W  # noqa: E402
+from paper_2410_09739_gb300 import fpclbm as F  # noqa: E402
+
+
+def parse(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--H", type=int, default=64, help="half-channel height in cells")
+    p.add_argument("--re-tau", type=float, default=180.0)
+    p.add_argument("--u-star", type=float, default=0.006)
+    p.add_argument("--cs", type=float, default=0.1, help="Smagorinsky constant")
+    p.add_argument("--a-plus", type=float, default=26.0, help="van Driest constant")
+    p.add_argument("--spinup", type=float, default=30.0, help="friction times before statistics")
+    p.add_argument("--collect", type=float, default=20.0, help="friction times of statistics")
+    p.add_argument("--every", type=int, default=200, help="steps between samples")
+    p.add_argument("--precision", default="fp32")
+    p.add_argument("--model", default="smagorinsky", choices=["smagorinsky", "none"])
+    p.add_argument("--seed", type=int, default=7)
+    return p.parse_args(argv)
+
+
+def run(args):
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    H = args.H
+    nx, ny, nz = int(round(2 * math.pi * H)), H, int(round(math.pi * H))
+    us = args.u_star
+    nu = us * H / args.re_tau
+    tau = 3.0 * nu + 0.5
+    Fx = us * us / H
+    Tstar = H / us
+    lat = F.Lattice(nx, ny, nz, args.precision, F.FPCLBM_BC_HALF_CHANNEL, stream=stream)
+    if args.model == "smagorinsky":
+        lat.set_params(tau, 0.0, F.FPCLBM_DIFF_FP_SMAGORINSKY)
+        lat.set_smagorinsky(args.cs, us, args.a_plus)
+    else:
+        lat.set_params(tau)
+    lat.set_force(Fx, 0.0, 0.0)
+    rho, ux, uy, uz = W.channel_fields(nx, 2 * ny, nz, us, seed=args.seed)
+    lat.init_fields(*(np.ascontiguousarray(a[:, :ny, :]) for a in (rho, ux, uy, uz)))
+
+    t0 = time.perf_counter()
+    n_spin = int(round(args.spinup * Tstar))
+    done = 0
+    while done < n_spin:
+        k = min(8192, n_spin - done)
+        lat.step(k)
+        done += k
+    spin_s = time.perf_counter() - t0
+
+    n = nx * ny * nz
+    buf = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
+    acc = {k: torch.zeros(ny, dtype=torch.float64, device="cuda") for k in ("u", "v", "w", "uu", "vv", "ww", "uv")}
+    n_coll = int(round(args.collect * Tstar))
+    samples = 0
+    t0 = time.perf_counter()
+    done = 0
+    while done < n_coll:
+        lat.step(args.every)
+        done += args.every
+        F.fpclbm_moments(lat.h, *buf, on_device=1)
+        u, v, w = (b.view(nz, ny, nx) for b in buf[1:])
+        acc["u"] += u.mean(dim=(0, 2))
+        acc["v"] += v.mean(dim=(0, 2))
+        acc["w"] += w.mean(dim=(0, 2))
+        acc["uu"] += (u * u).mean(dim=(0, 2))
+        acc["vv"] += (v * v).mean(dim=(0, 2))
+        acc["ww"] += (w * w).mean(dim=(0, 2))
+        acc["uv"] += (u * v).mean(dim=(0, 2))
+        samples += 1
+    torch.cuda.synchronize()
+    coll_s = time.perf_counter() - t0
+    m = {k: (a / samples).cpu().numpy() for k, a in acc.items()}
+    lat.close()
+
+    U, V, Wm = m["u"], m["v"], m["w"]
+    urms = np.sqrt(np.maximum(m["uu"] - U * U, 0))
+    vrms = np.sqrt(np.maximum(m["vv"] - V * V, 0))
+    wrms = np.sqrt(np.maximum(m["ww"] - Wm * Wm, 0))
+    uv = m["uv"] - U * V
+    y = np.arange(ny) + 0.5  # distance of the row centre from the wall
+    yplus = y * us / nu
+    uplus = U / us
+    law = np.where(yplus < 5, yplus, np.where(yplus > 30, np.log(np.maximum(yplus, 1e-30)) / 0.41 + 5.2, np.nan))
+    visc = (yplus < 5)
+    logr = (yplus > 30) & (yplus < 0.3 * args.re_tau)
+    # momentum balance: nu dU/dy - <u'v'> (+ subgrid) = u*^2 (1 - y/H); resolved part reported
+    dUdy = np.gradient(U, y)
+    resolved = nu * dUdy - uv
+    exact = us * us * (1 - y / H)
+    steps = n_spin + n_coll
+    return {
+        "study": "half-channel LES, FPC-LBM + Smagorinsky/van Driest",
+        "config": {"domain": [nx, ny, nz], "H": H, "re_tau": args.re_tau, "u_star": us, "nu": nu, "tau": tau,
+                   "Fx": Fx, "Cs": args.cs if args.model == "smagorinsky" else 0.0, "A_plus": args.a_plus,
+                   "friction_time_steps": Tstar, "spinup_T": args.spinup, "collect_T": args.collect,
+                   "samples": samples, "precision": args.precision, "model": args.model},
+        "bulk_velocity_over_u_star": float(np.mean(U) / us),
+        "centreline_u_plus": float(uplus[-1]),
+        "viscous_sublayer_max_abs_dev_u_plus": float(np.nanmax(np.abs(uplus[visc] - law[visc]))) if visc.any() else None,
+        "log_layer_max_abs_dev_u_plus": float(np.nanmax(np.abs(uplus[logr] - law[logr]))) if logr.any() else None,
+        "log_layer_rows": int(logr.sum()),
+        "resolved_stress_over_total_at_y_H_0p5": float(np.interp(0.5 * H, y, resolved / np.maximum(exact, 1e-30))),
+        "y_plus": [round(float(v), 3) for v in yplus],
+        "u_plus": [round(float(v), 4) for v in uplus],
+        "urms_plus": [round(float(v), 4) for v in urms / us],
+        "vrms_plus": [round(float(v), 4) for v in vrms / us],
+        "wrms_plus": [round(float(v), 4) for v in wrms / us],
+        "uv_plus": [round(float(v), 4) for v in -uv / us**2],
+        "seconds": {"spinup": spin_s, "collect": coll_s},
+        "mlups": n * steps / (spin_s + coll_s) / 1e6,
+    }
+
+
+def main(argv=None):
+    print(json.dumps(run(parse(argv))))
+
+
+if __name__ == "__main__":
+    main()

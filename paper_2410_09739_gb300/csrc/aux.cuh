@@ -15,7 +15,7 @@ __device__ __forceinline__ void cell_xyz(const BoxGeom& b, unsigned cell, unsign
 
 // Deviations g_s(x) at the current time, whatever the AA parity.
 // parity 0: buf[s][x]; parity 1: buf[26-s][x - e_s], or buf[s][x] when the
-// source lies in a y wall (see cell.cuh).
+// source lies in a wall (see cell.cuh).
 template <typename S>
 __device__ void load_cell(const BoxGeom& b, int parity, unsigned cell, double g[27])
 {
@@ -29,8 +29,15 @@ __device__ void load_cell(const BoxGeom& b, int parity, unsigned cell, double g[
     const int nx = b.nx, ny = b.ny, nz = b.nz;
     for (int s = 0; s < 27; ++s) {
         const int ex = s % 3 - 1, ey = (s / 3) % 3 - 1, ez = s / 9 - 1;
-        const int sy = (int)y - ey;
-        if (b.walls && (sy < 0 || sy >= ny)) {
+        const int sx0 = (int)x - ex, sy = (int)y - ey, sz0 = (int)z - ez;
+        if (b.walls == 3 && sy >= ny) {  // half channel: specular through the symmetry plane
+            const int mx = (sx0 + nx) % nx, mz = (sz0 + nz) % nz;
+            g[s] = Store<S>::ldd(buf + (size_t)(20 - s) * b.stride + (size_t)mx + (size_t)nx * ((size_t)y + (size_t)ny * mz));
+            continue;
+        }
+        const bool out_y = b.walls >= 1 && (sy < 0 || sy >= ny);
+        const bool out_xz = b.walls == 2 && (sx0 < 0 || sx0 >= nx || sz0 < 0 || sz0 >= nz);
+        if (out_y || out_xz) {
             g[s] = Store<S>::ldd(buf + (size_t)s * b.stride + cell);
             continue;
         }

@@ -6,12 +6,26 @@
 //   odd step:  read buf[26-s][x - e_s] (the streamed value of Step 6),
 //              collide, write buf[s][x + e_s].
 // Each thread reads and writes the same 27 addresses in both parities, so
-// the update is race-free without a second buffer.  Half-way bounce-back on
-// y walls: an odd-step read whose source x - e_s lies in a wall takes
-// buf[s][x] (the reflected post-collision value parked there by the even
-// step), and an odd-step write whose destination x + e_s lies in a wall goes
-// to buf[26-s][x], where the next even step reads it as the reflected
-// population.  Periodic wrap in x, z (and y without walls).
+// the update is race-free without a second buffer.  Half-way bounce-back
+// (y walls, or all six faces of a closed box): an odd-step read whose source
+// x - e_s lies in a wall takes buf[s][x] (the reflected post-collision value
+// parked there by the even step), and an odd-step write whose destination
+// x + e_s lies in a wall goes to buf[26-s][x], where the next even step reads
+// it as the reflected population.  Periodic wrap on the other axes.
+//
+// Symmetry plane y = ny - 1/2 of the half channel (Sec. 4, turbulent channel):
+// a population leaving the top row along (ex, +1, ez) comes back along
+// (ex, -1, ez) at x + (ex, 0, ez) (specular reflection).  Only the odd step
+// sees it: the read of slot s (e_y = -1) of a top-row cell takes the value
+// parked by the even step at x - (ex, 0, ez) in slot 20 - s (the opposite of
+// the mirror image of s), and the write of slot s (e_y = +1) goes to slot
+// s - 6 (its mirror image) at x + (ex, 0, ez), the address the receiving
+// thread read for that slot, so the in-place update stays race-free.
+//
+// Moving wall y = ny - 1/2 (Sec. 4, cubic cavity): a post-collision value of
+// a top-row cell with e_y = +1 is reflected by that wall in either parity, so
+// the momentum correction -2 w_s rho (e_s . u_w) / cs^2 is applied to it just
+// before it is stored, with rho the cell's density.
 //
 // Traffic per cell update: 27 reads + 27 writes of the storage type.
 #pragma once
@@ -28,15 +42,16 @@ struct CellGeom {
 
 // Neighbour coordinates of a cell for the odd step: column, row offset and
 // plane offset of x - e for e = -1, 0, +1 (index 0, 1, 2), and whether the
-// source row lies inside the fluid (y walls).
+// source lies inside the fluid on each axis (walls).
 struct Nbr {
-    unsigned xs[3], yr[3], zp[3];
-    bool yin[3];
+    unsigned xs[3], yz[3][3];  // column of x - e_x; row + plane offset of (y - e_y, z - e_z)
+    bool xin[3], yin[3], zin[3];
 };
 
-template <bool WALLS>
+template <int BC>
 __device__ __forceinline__ Nbr make_nbr(const CellGeom& G, unsigned cell)
 {
+    constexpr bool WY = BC != BC_PERIODIC, WXZ = BC == BC_BOX_LID;  // half channel: rows tested like walls
     Nbr n;
     const unsigned nx = G.nx, ny = G.ny, nz = G.nz, nxny = nx * ny;
     const unsigned z = fdiv(cell, G.div_nxny);
@@ -46,59 +61,110 @@ __device__ __forceinline__ Nbr make_nbr(const CellGeom& G, unsigned cell)
     n.xs[0] = (x + 1 == nx) ? 0u : x + 1;
     n.xs[1] = x;
     n.xs[2] = (x == 0) ? nx - 1 : x - 1;
+    n.xin[0] = WXZ ? (x + 1 < nx) : true;
+    n.xin[1] = true;
+    n.xin[2] = WXZ ? (x > 0) : true;
     const unsigned yp = (y + 1 == ny) ? 0u : y + 1, ym = (y == 0) ? ny - 1 : y - 1;
-    n.yr[0] = yp * nx;
-    n.yr[1] = y * nx;
-    n.yr[2] = ym * nx;
-    n.yin[0] = WALLS ? (y + 1 < ny) : true;
+    const unsigned yr[3] = {yp * nx, y * nx, ym * nx};
+    n.yin[0] = WY ? (y + 1 < ny) : true;
     n.yin[1] = true;
-    n.yin[2] = WALLS ? (y > 0) : true;
+    n.yin[2] = WY ? (y > 0) : true;
+    n.zin[0] = WXZ ? (z + 1 < nz) : true;
+    n.zin[1] = true;
+    n.zin[2] = WXZ ? (z > 0) : true;
     const unsigned zpp = (z + 1 == nz) ? 0u : z + 1, zmm = (z == 0) ? nz - 1 : z - 1;
-    n.zp[0] = zpp * nxny;
-    n.zp[1] = z * nxny;
-    n.zp[2] = zmm * nxny;
+    const unsigned zp[3] = {zpp * nxny, z * nxny, zmm * nxny};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) n.yz[j][k] = yr[j] + zp[k];
     return n;
 }
 
 // Address read for slot s (the population that streams into the cell).  The
 // slot row base buf + row * stride is the same for the whole warp, so it is
 // formed separately from the per-thread cell offset (uniform-register base).
-template <typename S, bool ODD, bool WALLS>
+// Whether the point x - e (index i = e + 1 per axis) lies inside the fluid.
+template <int BC>
+__device__ __forceinline__ bool inside(const Nbr& n, int ix, int iy, int iz)
+{
+    if (BC == BC_PERIODIC) return true;
+    if (BC == BC_BOX_LID) return n.xin[ix] && n.yin[iy] && n.zin[iz];
+    return n.yin[iy];
+}
+
+template <typename S, bool ODD, int BC>
 __device__ __forceinline__ S* load_ptr(S* buf, int s, const Nbr& n, unsigned stride, unsigned cell)
 {
     if (!ODD) return buf + (size_t)s * stride + cell;
     const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
-    if (WALLS && !n.yin[iy]) return buf + (size_t)s * stride + cell;
-    return buf + (size_t)(26 - s) * stride + (n.xs[ix] + n.yr[iy] + n.zp[iz]);
+    if (BC == BC_HALF_CHANNEL && iy == 0 && !n.yin[0])  // specular, through the symmetry plane
+        return buf + (size_t)(20 - s) * stride + (n.xs[ix] + n.yz[1][iz]);
+    if (!inside<BC>(n, ix, iy, iz)) return buf + (size_t)s * stride + cell;
+    return buf + (size_t)(26 - s) * stride + (n.xs[ix] + n.yz[iy][iz]);
 }
 
 // Address written for slot s (the destination of the post-collision value).
-template <typename S, bool ODD, bool WALLS>
+template <typename S, bool ODD, int BC>
 __device__ __forceinline__ S* store_ptr(S* buf, int s, const Nbr& n, unsigned stride, unsigned cell)
 {
     if (!ODD) return buf + (size_t)(26 - s) * stride + cell;
     const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
-    if (WALLS && !n.yin[2 - iy]) return buf + (size_t)(26 - s) * stride + cell;
-    return buf + (size_t)s * stride + (n.xs[2 - ix] + n.yr[2 - iy] + n.zp[2 - iz]);
+    if (BC == BC_HALF_CHANNEL && iy == 2 && !n.yin[0])  // specular, through the symmetry plane
+        return buf + (size_t)(s - 6) * stride + (n.xs[2 - ix] + n.yz[1][2 - iz]);
+    if (!inside<BC>(n, 2 - ix, 2 - iy, 2 - iz)) return buf + (size_t)(26 - s) * stride + cell;
+    return buf + (size_t)s * stride + (n.xs[2 - ix] + n.yz[2 - iy][2 - iz]);
 }
 
-template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE>
+// Moving-wall correction of the post-collision values of a top-row cell:
+// g_s -= w_s rho (e_s . u_w) 2 / cs^2 for the nine slots with e_y = +1.
+template <typename R>
+__device__ __forceinline__ void lid_correct(R g[27], R lid6x, R lid6z)
+{
+    R rho = R(1);
+#pragma unroll
+    for (int s = 0; s < 27; ++s) rho += g[s];
+#pragma unroll
+    for (int s = 6; s < 9; ++s) {  // e_y = +1, e_z = -1
+        const R ex = R(s % 3 - 1);
+        g[s] -= R(wslot(s)) * rho * (ex * lid6x - lid6z);
+        g[s + 9] -= R(wslot(s + 9)) * rho * (ex * lid6x);
+        g[s + 18] -= R(wslot(s + 18)) * rho * (ex * lid6x + lid6z);
+    }
+}
+
+// active = false: the lane only takes part in warp-collective work (learned
+// mode); it reads a valid cell but writes nothing.
+template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE>
 __device__ __forceinline__ void update_cell(S* __restrict__ buf, const CellGeom& G, unsigned cell,
                                             const Rates<R>& rt, R Fx, R Fy, R Fz, R om4, R om5, R om6, R om8,
-                                            R om9, const float* closure, int* flag)
+                                            R om9, const float* closure, int* flag, bool active = true,
+                                            R lid6x = R(0), R lid6z = R(0), const R* smag = nullptr)
 {
     const unsigned stride = G.stride;
     R g[27];
     Nbr n;
-    if (ODD) n = make_nbr<WALLS>(G, cell);
+    if (ODD) n = make_nbr<BC>(G, cell);
 #pragma unroll
-    for (int s = 0; s < 27; ++s) g[s] = Store<S>::ld(load_ptr<S, ODD, WALLS>(buf, s, n, stride, cell));
+    for (int s = 0; s < 27; ++s) g[s] = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, cell));
 
-    const bool ok = collide_cell<R, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, closure);
-    if (!ok) atomicOr(flag, 1);
+    R c2 = R(0);  // Smagorinsky: (C_s Delta D(y))^2 of this cell's row
+    if (MODE == MODE_SMAG) c2 = smag[fdiv(cell - fdiv(cell, G.div_nxny) * (unsigned)(G.nx * G.ny), G.div_nx)];
+    const bool ok = collide_cell<R, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, closure, c2);
+    if (!ok && active) atomicOr(flag, 1);
 
+    // rebuild the store addresses (and the odd step's neighbour table) instead of keeping
+    // the load addresses live through the collision: the empty asm hides that cell is
+    // unchanged, so the compiler cannot keep the old copies in registers
+    asm volatile("" : "+r"(cell));
+    if (ODD) n = make_nbr<BC>(G, cell);
+    if (!active) return;
+    if (BC == BC_WALLS_Y_LID || BC == BC_BOX_LID) {
+        const unsigned y = fdiv(cell - fdiv(cell, G.div_nxny) * (unsigned)(G.nx * G.ny), G.div_nx);
+        if (y + 1 == (unsigned)G.ny) lid_correct(g, lid6x, lid6z);
+    }
 #pragma unroll
-    for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, WALLS>(buf, s, n, stride, cell), g[s]);
+    for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, cell), g[s]);
 }
 
 }  // namespace fpc

@@ -343,6 +343,8 @@ extern "C" int fpclbm_closure_sample(fpclbm_t h, int r, double tau_coarse, float
     if (!X || !T) return fail(h, FPCLBM_ERR_ARG, "null output");
     if (!(tau_coarse > 0.5) || !std::isfinite(tau_coarse)) return fail(h, FPCLBM_ERR_ARG, "tau_coarse must be > 1/2");
     const int cx = B.nx / r, cy = B.ny / r, cz = B.nz / r;
+    if (h->bc != FPCLBM_BC_PERIODIC && h->bc != FPCLBM_BC_WALLS_Y)
+        return fail(h, FPCLBM_ERR_ARG, "closure sampling needs a periodic or channel box");
     const bool walls = h->bc == FPCLBM_BC_WALLS_Y;
     if (walls && cy < 2) return fail(h, FPCLBM_ERR_ARG, "walls need ny / r >= 2");
     const size_t nc = (size_t)cx * cy * cz;

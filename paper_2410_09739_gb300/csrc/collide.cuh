@@ -92,18 +92,19 @@ __device__ __forceinline__ void inv3(R& k0, R& k1, R& k2, R u, R u2, R tu, R K)
     }
 
 // Per-cell learned correction of the shear rates (mode LEARNED): MLP
-// 9 -> 64 -> 64 -> 1 with tanh hidden layers, fp32 weights in W (layout of
-// fpclbm_set_closure).  Implemented in closure.cuh.
+// 9 -> 64 -> 64 -> 1 with tanh hidden layers on the tensor cores, weights
+// packed by fpclbm_set_closure.  Warp-collective; implemented in closure.cuh.
 template <typename R>
-__device__ R closure_delta_omega(const float* W, const R in[9]);
+__device__ R closure_delta_omega(const uint32_t* P, const R in[9]);
 
 // Collide one cell in place.  rt: rates of Step 3; Fx, Fy, Fz: body force;
 // om4..om9: the five shear rates (110, 101, 011, 2d1, 2d2), given separately
 // because ensembles carry one shear rate per box; closure: MLP weights
-// (learned mode only).  Returns false when rho <= 0 or not finite.
+// (learned mode only); c2 = (C_s Delta D)^2 of the cell (Smagorinsky mode
+// only).  Returns false when rho <= 0 or not finite.
 template <typename R, bool FORCE, int MODE>
 __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R Fx, R Fy, R Fz, R om4, R om5, R om6,
-                                             R om8, R om9, const float* closure)
+                                             R om8, R om9, const float* closure, R c2 = R(0))
 {
     // ---- Step 7 and the first pass (z lines), sharing the line sums ----
     R S[9], Dz[9], Pz[9];
@@ -167,13 +168,31 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
         in[6] = ux;
         in[7] = uy;
         in[8] = uz;
-        const R dw = closure_delta_omega<R>(closure, in);
+        const R dw = closure_delta_omega<R>(reinterpret_cast<const uint32_t*>(closure), in);
         const R lo = R(0.02), hi = R(1.98);
         om4 = fmin(fmax(om4 + dw, lo), hi);
         om5 = fmin(fmax(om5 + dw, lo), hi);
         om6 = fmin(fmax(om6 + dw, lo), hi);
         om8 = fmin(fmax(om8 + dw, lo), hi);
         om9 = fmin(fmax(om9 + dw, lo), hi);
+    }
+
+    // Smagorinsky eddy viscosity (Sec. 4, turbulent channel LES): nu_t = c2 |S|, the strain rate
+    // from the deviatoric non-equilibrium second moments Pi^d at the effective time tau,
+    // S = -Pi^d / (2 rho cs^2 tau), tau = tau0 + nu_t / cs^2; the positive root of
+    // tau^2 - tau0 tau - c2 |Pi^d| / (2 rho cs^4) = 0 replaces all five shear rates.
+    if constexpr (MODE == MODE_SMAG) {
+        const R p0 = FPC_D(2, 0, 0) - third * drho, p1 = FPC_D(0, 2, 0) - third * drho;
+        const R p2 = FPC_D(0, 0, 2) - third * drho;
+        const R tr = third * ((p0 + p1) + p2);
+        const R q0 = p0 - tr, q1 = p1 - tr, q2 = p2 - tr;
+        const R o1 = FPC_D(1, 1, 0), o2 = FPC_D(1, 0, 1), o3 = FPC_D(0, 1, 1);
+        const R pp = fmaR(q0, q0, fmaR(q1, q1, q2 * q2)) + R(2) * fmaR(o1, o1, fmaR(o2, o2, o3 * o3));
+        const R Pn = sqrt(R(2) * pp);
+        const R tau0 = R(1) / om4;
+        const R te = R(0.5) * (tau0 + sqrt(fmaR(tau0, tau0, R(18) * c2 * Pn * inv_rho)));
+        const R w = R(1) / te;
+        om4 = om5 = om6 = om8 = om9 = w;
     }
 
     // order 1 (attractor 0, source F).  In exact arithmetic kappa_100 = -F_x/2 and

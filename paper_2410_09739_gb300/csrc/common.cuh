@@ -16,8 +16,20 @@
 namespace fpc {
 
 // Attractor modes of the collision: FP diffusion tensor, Maxwellian (MCM),
-// FP with the learned shear-rate correction.
-enum { MODE_FP = 0, MODE_EQ = 1, MODE_LEARNED = 2 };
+// FP with the learned shear-rate correction, FP with the Smagorinsky eddy
+// viscosity (van Driest damped) in the shear rates.
+enum { MODE_FP = 0, MODE_EQ = 1, MODE_LEARNED = 2, MODE_SMAG = 3 };
+
+// Boundary kinds of the step kernel: periodic box; half-way bounce-back walls
+// at y = -1/2 and ny - 1/2 (x, z periodic); the same with the wall at
+// y = ny - 1/2 moving; closed box (bounce-back on all six faces) whose wall
+// at y = ny - 1/2 moves (lid-driven cavity; the lid may be at rest); half
+// channel: bounce-back wall at y = -1/2, specular-reflection symmetry plane
+// at y = ny - 1/2 (x, z periodic).
+enum { BC_PERIODIC = 0, BC_WALLS_Y = 1, BC_WALLS_Y_LID = 2, BC_BOX_LID = 3, BC_HALF_CHANNEL = 4 };
+
+// Boundary kinds whose walls rest and that have the register-cap variants.
+__host__ __device__ constexpr bool bc_fixed(int bc) { return bc == BC_PERIODIC || bc == BC_WALLS_Y || bc == BC_HALF_CHANNEL; }
 
 // Unsigned division by a runtime constant d < 2^31 for numerators n < 2^31:
 // q = (umulhi(n, m) + n) >> s with s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1
@@ -62,9 +74,11 @@ struct StepArgs {
     int nx, ny, nz;
     FastDiv div_nx, div_nxny;
     R Fx, Fy, Fz;         // body force
+    R lid6x, lid6z;       // 2 / cs^2 = 6 times the velocity of the wall y = ny - 1/2 (BC_*_LID)
     Rates<R> rates;
     int* flag;            // set to 1 by any cell with rho <= 0 or non-finite
-    const float* closure; // fp32 copy of the MLP weights (learned mode), else null
+    const float* closure; // packed MLP weights (learned mode), else null
+    const R* smag;        // (C_s Delta D(y))^2 per row y (Smagorinsky mode), else null
 };
 
 // Storage traits: load as compute type R, store from R with round-to-nearest.

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256, MINB) k_ens_step(const EnsArgs a)
         for (unsigned c = threadIdx.x; c < a.tile_cells; c += blockDim.x) {
             const unsigned cell = first + c;
             if (cell >= ncells) break;
-            update_cell<float, float, ODD, false, FORCE, MODE>(buf, G, cell, a.rates, a.Fx, a.Fy, a.Fz, om, om, om, om,
+            update_cell<float, float, ODD, BC_PERIODIC, FORCE, MODE>(buf, G, cell, a.rates, a.Fx, a.Fy, a.Fz, om, om, om, om,
                                                                om, nullptr, a.flag);
         }
     }

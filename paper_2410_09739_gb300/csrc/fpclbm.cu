@@ -7,6 +7,7 @@
 // On the first fpclbm_step of a large enough handle the launch configuration
 // is autotuned on a saved copy of the state (the state is restored bit for
 // bit afterwards), and the choice is cached per device and configuration.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -16,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "closure.cuh"
 #include "handle.h"
 
 using namespace fpc;
@@ -135,6 +137,8 @@ StepArgs<R> make_args(const fpclbm* h)
     a.Fx = (R)h->F[0];
     a.Fy = (R)h->F[1];
     a.Fz = (R)h->F[2];
+    a.lid6x = (R)(6.0 * h->lid[0]);
+    a.lid6z = (R)(6.0 * h->lid[1]);
     for (int j = 0; j < 27; ++j) {
         a.rates.om[j] = (R)h->omega[j];
         a.rates.keep[j] = (R)(1.0 - h->omega[j]);
@@ -142,6 +146,7 @@ StepArgs<R> make_args(const fpclbm* h)
     }
     a.flag = h->d_flag;
     a.closure = h->d_closure;
+    a.smag = h->diffusion == FPCLBM_DIFF_FP_SMAGORINSKY ? static_cast<const R*>(h->d_smag) : nullptr;
     return a;
 }
 
@@ -174,7 +179,7 @@ BoxGeom geom_of(const fpclbm* h, const Box& b)
     g.nx = b.nx;
     g.ny = b.ny;
     g.nz = b.nz;
-    g.walls = h->bc == FPCLBM_BC_WALLS_Y;
+    g.walls = h->bc == FPCLBM_BC_WALLS_Y ? 1 : h->bc == FPCLBM_BC_BOX ? 2 : h->bc == FPCLBM_BC_HALF_CHANNEL ? 3 : 0;
     g.div_nx = make_fastdiv((unsigned)b.nx);
     g.div_nxny = make_fastdiv((unsigned)(b.nx * b.ny));
     return g;
@@ -184,10 +189,53 @@ int mode_of(const fpclbm* h)
 {
     if (h->diffusion == FPCLBM_DIFF_EQUILIBRIUM) return MODE_EQ;
     if (h->diffusion == FPCLBM_DIFF_FP_LEARNED) return MODE_LEARNED;
+    if (h->diffusion == FPCLBM_DIFF_FP_SMAGORINSKY) return MODE_SMAG;
     return MODE_FP;
 }
 
 bool has_force(const fpclbm* h) { return h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0; }
+
+// Boundary kind of the step kernel: a channel whose upper wall moves takes the
+// moving-wall variant; a closed box always does (its lid may rest).
+int kernel_bc(const fpclbm* h)
+{
+    if (h->bc == FPCLBM_BC_BOX) return BC_BOX_LID;
+    if (h->bc == FPCLBM_BC_HALF_CHANNEL) return BC_HALF_CHANNEL;
+    if (h->bc == FPCLBM_BC_WALLS_Y) return (h->lid[0] != 0.0 || h->lid[1] != 0.0) ? BC_WALLS_Y_LID : BC_WALLS_Y;
+    return BC_PERIODIC;
+}
+
+// (C_s Delta D(y))^2 per row y (Delta = 1): van Driest damping D = 1 - exp(-y+ / A+),
+// y+ = y_w u* / nu, y_w the distance of the row centre to the nearest wall (none in a
+// periodic box; u* <= 0 or A+ <= 0 switch the damping off).  nu from the shear rate omega_4.
+int upload_smag(fpclbm* h)
+{
+    const Box& b = h->boxes[0];
+    const int ny = b.ny;
+    if (!h->d_smag) {
+        cudaError_t e = cudaMalloc(&h->d_smag, sizeof(double) * (size_t)ny);
+        if (e != cudaSuccess) return fail(h, FPCLBM_ERR_ALLOC, std::string("Smagorinsky table: ") + cudaGetErrorString(e));
+    }
+    const double nu = (1.0 / h->omega[4] - 0.5) / 3.0;
+    std::vector<double> c2(ny);
+    std::vector<float> c2f(ny);
+    for (int y = 0; y < ny; ++y) {
+        double yw = -1.0;
+        if (h->bc == FPCLBM_BC_WALLS_Y) yw = std::min(y + 0.5, ny - 0.5 - y);
+        if (h->bc == FPCLBM_BC_HALF_CHANNEL) yw = y + 0.5;
+        double D = 1.0;
+        if (yw >= 0 && h->smag[1] > 0 && h->smag[2] > 0) D = 1.0 - std::exp(-(yw * h->smag[1] / nu) / h->smag[2]);
+        c2[y] = (h->smag[0] * D) * (h->smag[0] * D);
+        c2f[y] = (float)c2[y];
+    }
+    const bool f64 = h->precision == FPCLBM_FP64;
+    FPC_CK(h, cudaMemcpyAsync(h->d_smag, f64 ? (const void*)c2.data() : (const void*)c2f.data(),
+                              (f64 ? sizeof(double) : sizeof(float)) * (size_t)ny, cudaMemcpyHostToDevice, h->stream),
+           "Smagorinsky table upload");
+    FPC_CK(h, cudaStreamSynchronize(h->stream), "Smagorinsky table upload");
+    h->smag_dirty = false;
+    return FPCLBM_OK;
+}
 
 cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st, int block, int minb, int grid, int pipe)
 {
@@ -196,8 +244,7 @@ cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st, int block, int min
     const StepArgs<double> a64 = make_args<double>(h);
     const StepArgs<float> a32 = make_args<float>(h);
     StepLaunch cfg{block, minb, pipe};
-    return launch_step(h->precision, (int)(t & 1), h->bc == FPCLBM_BC_WALLS_Y, has_force(h), mode_of(h), a64, a32, cfg,
-                       st);
+    return launch_step(h->precision, (int)(t & 1), kernel_bc(h), has_force(h), mode_of(h), a64, a32, cfg, st);
 }
 
 void drop_graph(fpclbm* h)
@@ -307,7 +354,7 @@ bool forced_launch(TuneChoice& c)
 std::string tune_key(const fpclbm* h)
 {
     char buf[160];
-    std::snprintf(buf, sizeof buf, "dev%d/p%d/bc%d/f%d/m%d/%s/%llu", h->device, h->precision, h->bc, (int)has_force(h),
+    std::snprintf(buf, sizeof buf, "dev%d/p%d/bc%d/f%d/m%d/%s/%llu", h->device, h->precision, kernel_bc(h), (int)has_force(h),
                   mode_of(h), h->ensemble ? "ens" : "box", (unsigned long long)(h->total_cells >> 20));
     return buf;
 }
@@ -316,8 +363,13 @@ int autotune(fpclbm* h)
 {
     h->tuned = true;
     std::vector<TuneChoice> cands;
-    const bool fp32_math = h->precision != FPCLBM_FP64 && mode_of(h) != MODE_LEARNED;
-    const bool pipe_ok = elem_size(h->precision) >= 4;  // cp.async moves >= 4 bytes
+    // register-cap variants: fp32 arithmetic, FP/EQ modes, resting walls; pipelined variant: the
+    // same on periodic and channel boxes with 4- or 8-byte storage (cp.async moves >= 4 bytes)
+    const int kb = kernel_bc(h), md = mode_of(h);
+    const bool fixed_walls = bc_fixed(kb);
+    const bool fp32_math = h->precision != FPCLBM_FP64 && (md == MODE_FP || md == MODE_EQ) && fixed_walls;
+    const bool pipe_ok = elem_size(h->precision) >= 4 && (md == MODE_FP || md == MODE_EQ) &&
+                         (kb == BC_PERIODIC || kb == BC_WALLS_Y);
     if (h->ensemble) {
         for (int minb : {2, 3})
             for (int block : {128, 256}) {
@@ -329,14 +381,18 @@ int autotune(fpclbm* h)
             for (int block : {128, 256}) cands.push_back({block, minb, 0, 0});
         if (pipe_ok)
             for (int minb : {2, 3, 4}) cands.push_back({128, minb, 0, 1});
+    } else if (mode_of(h) == MODE_LEARNED && h->precision != FPCLBM_FP64 && fixed_walls) {
+        // capped at 128 registers first: twice the resident warps of the uncapped variant
+        for (int minb : {2, 1})
+            for (int block : {128, 256}) cands.push_back({block, minb, 0, 0});
     } else {
         for (int block : {128, 256}) cands.push_back({block, 1, 0, 0});
-        if (pipe_ok && mode_of(h) != MODE_LEARNED) cands.push_back({128, 1, 0, 1});
+        if (pipe_ok) cands.push_back({128, 1, 0, 1});
     }
     TuneChoice forced;
     if (!h->ensemble && forced_launch(forced)) {
         if (forced.pipe && !pipe_ok) forced.pipe = 0;
-        if (!fp32_math) forced.minb = 1;
+        if (!fp32_math && mode_of(h) != MODE_LEARNED) forced.minb = 1;  // learned: 1 or 2 (else 1)
         h->block = forced.block;
         h->minb = forced.minb;
         h->grid = 0;
@@ -439,7 +495,7 @@ int fpclbm_create(fpclbm_t* out, int nx, int ny, int nz, int precision, int bc, 
         g_create_error = "unknown precision";
         return FPCLBM_ERR_ARG;
     }
-    if (bc != FPCLBM_BC_PERIODIC && bc != FPCLBM_BC_WALLS_Y) {
+    if (bc != FPCLBM_BC_PERIODIC && bc != FPCLBM_BC_WALLS_Y && bc != FPCLBM_BC_BOX && bc != FPCLBM_BC_HALF_CHANNEL) {
         g_create_error = "unknown boundary condition";
         return FPCLBM_ERR_ARG;
     }
@@ -488,6 +544,7 @@ int fpclbm_destroy(fpclbm_t h)
     if (h->d_diag) cudaFree(h->d_diag);
     if (h->h_diag) cudaFreeHost(h->h_diag);
     if (h->d_closure) cudaFree(h->d_closure);
+    if (h->d_smag) cudaFree(h->d_smag);
     if (h->d_ens_boxes) cudaFree(h->d_ens_boxes);
     if (h->d_tile_box) cudaFree(h->d_tile_box);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -546,8 +603,10 @@ int fpclbm_set_params(fpclbm_t h, double tau, double drift, int diffusion)
 {
     if (!h) return FPCLBM_ERR_ARG;
     h->err.clear();
-    if (diffusion < FPCLBM_DIFF_FP || diffusion > FPCLBM_DIFF_FP_LEARNED)
+    if (diffusion < FPCLBM_DIFF_FP || diffusion > FPCLBM_DIFF_FP_SMAGORINSKY)
         return fail(h, FPCLBM_ERR_ARG, "unknown diffusion mode");
+    if (diffusion == FPCLBM_DIFF_FP_SMAGORINSKY && h->ensemble)
+        return fail(h, FPCLBM_ERR_ARG, "Smagorinsky mode is for single boxes");
     if (!std::isfinite(tau) || !std::isfinite(drift) || drift < 0)
         return fail(h, FPCLBM_ERR_ARG, "tau and drift must be finite, drift >= 0");
     if (diffusion == FPCLBM_DIFF_FP_LEARNED && !h->have_closure)
@@ -562,6 +621,7 @@ int fpclbm_set_params(fpclbm_t h, double tau, double drift, int diffusion)
     h->diffusion = diffusion;
     h->graph_valid = false;
     h->tuned = false;
+    h->smag_dirty = true;
     return FPCLBM_OK;
 }
 
@@ -575,6 +635,7 @@ int fpclbm_set_rates(fpclbm_t h, const double omega[27])
     if (!rates_valid(omega, why)) return fail(h, FPCLBM_ERR_PARAM, why);
     std::memcpy(h->omega, omega, sizeof(double) * 27);
     h->graph_valid = false;
+    h->smag_dirty = true;
     return FPCLBM_OK;
 }
 
@@ -592,6 +653,34 @@ int fpclbm_set_force(fpclbm_t h, double Fx, double Fy, double Fz)
     return FPCLBM_OK;
 }
 
+int fpclbm_set_smagorinsky(fpclbm_t h, double cs, double u_star, double a_plus)
+{
+    if (!h) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    if (h->ensemble) return fail(h, FPCLBM_ERR_ARG, "Smagorinsky model is for single boxes");
+    if (!std::isfinite(cs) || !std::isfinite(u_star) || !std::isfinite(a_plus) || cs < 0)
+        return fail(h, FPCLBM_ERR_ARG, "C_s must be finite and >= 0, u* and A+ finite");
+    h->smag[0] = cs;
+    h->smag[1] = u_star;
+    h->smag[2] = a_plus;
+    h->smag_dirty = true;
+    return FPCLBM_OK;
+}
+
+int fpclbm_set_wall_velocity(fpclbm_t h, double ux, double uz)
+{
+    if (!h) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    if (h->ensemble || (h->bc != FPCLBM_BC_WALLS_Y && h->bc != FPCLBM_BC_BOX))
+        return fail(h, FPCLBM_ERR_ARG, "wall velocity needs a box with walls (FPCLBM_BC_WALLS_Y or FPCLBM_BC_BOX)");
+    if (!std::isfinite(ux) || !std::isfinite(uz)) return fail(h, FPCLBM_ERR_ARG, "wall velocity must be finite");
+    h->lid[0] = ux;
+    h->lid[1] = uz;
+    h->graph_valid = false;
+    h->tuned = false;
+    return FPCLBM_OK;
+}
+
 int fpclbm_step(fpclbm_t h, long long n)
 {
     if (!h) return FPCLBM_ERR_ARG;
@@ -599,6 +688,17 @@ int fpclbm_step(fpclbm_t h, long long n)
     if (n < 0) return fail(h, FPCLBM_ERR_ARG, "negative step count");
     if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
     if (n == 0) return FPCLBM_OK;
+    {
+        const int kb = kernel_bc(h), md = mode_of(h);
+        if (md == MODE_LEARNED && !(kb == BC_PERIODIC || kb == BC_WALLS_Y))
+            return fail(h, FPCLBM_ERR_ARG, "learned mode needs a periodic box or a channel with resting walls");
+        if (md == MODE_SMAG && !bc_fixed(kb))
+            return fail(h, FPCLBM_ERR_ARG, "Smagorinsky mode needs resting walls (no closed box, no moving wall)");
+        if (md == MODE_SMAG && h->smag_dirty) {
+            int rc = upload_smag(h);
+            if (rc) return rc;
+        }
+    }
     if (!h->tuned) {
         int rc = autotune(h);
         if (rc) return rc;
@@ -806,19 +906,43 @@ int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
     h->err.clear();
     if (!w) return fail(h, FPCLBM_ERR_ARG, "weights are NULL");
     if (n_params != 4865) return fail(h, FPCLBM_ERR_ARG, "closure needs exactly 4865 parameters");
-    std::vector<float> wf(n_params);
     for (int i = 0; i < n_params; ++i) {
         const unsigned bits = (unsigned)w[i] << 16;  // bf16 -> fp32 is exact
         float v;
         std::memcpy(&v, &bits, sizeof v);
         if (!std::isfinite(v)) return fail(h, FPCLBM_ERR_ARG, "non-finite closure weight");
-        wf[i] = v;
     }
+    // re-pack into the per-lane mma fragment order of closure.cuh: for lane (g = lane/4,
+    // t = lane%4) and n-tile nt, output n = 8 nt + g; a 32-bit word holds two bf16 of
+    // consecutive k (lower k in the low half): k = 2t, 2t+1 and k = 2t+8, 2t+9
+    std::vector<uint32_t> pk(CP_WORDS, 0u);
+    auto wb = [&](int idx) -> uint32_t { return w[idx]; };
+    auto w1 = [&](int n, int k) -> uint32_t { return k < 9 ? wb(CL_W1 + 9 * n + k) : 0u; };
+    auto w2 = [&](int n, int k) -> uint32_t { return wb(CL_W2 + 64 * n + k); };
+    for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane / 4, t = lane % 4;
+        for (int nt = 0; nt < 8; ++nt) {
+            const int n = 8 * nt + g;
+            pk[CP_F1 + (nt * 32 + lane) * 2] = w1(n, 2 * t) | (w1(n, 2 * t + 1) << 16);
+            pk[CP_F1 + (nt * 32 + lane) * 2 + 1] = w1(n, 2 * t + 8) | (w1(n, 2 * t + 9) << 16);
+            for (int kt = 0; kt < 4; ++kt) {
+                const int k = 16 * kt + 2 * t;
+                pk[CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2] = w2(n, k) | (w2(n, k + 1) << 16);
+                pk[CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2 + 1] = w2(n, k + 8) | (w2(n, k + 9) << 16);
+            }
+        }
+    }
+    for (int j = 0; j < 64; ++j) {
+        pk[CP_B1 + j] = wb(CL_B1 + j) << 16;  // fp32 bit patterns of the bf16 values
+        pk[CP_B2 + j] = wb(CL_B2 + j) << 16;
+        pk[CP_W3 + j] = wb(CL_W3 + j) << 16;
+    }
+    pk[CP_B3] = wb(CL_B3) << 16;
     if (!h->d_closure) {
-        cudaError_t e = cudaMalloc(&h->d_closure, sizeof(float) * 4868);  // 16-byte padded
+        cudaError_t e = cudaMalloc(&h->d_closure, sizeof(uint32_t) * CP_WORDS);
         if (e != cudaSuccess) return fail(h, FPCLBM_ERR_ALLOC, "closure weights");
     }
-    FPC_CK(h, cudaMemcpyAsync(h->d_closure, wf.data(), sizeof(float) * n_params, cudaMemcpyHostToDevice, h->stream),
+    FPC_CK(h, cudaMemcpyAsync(h->d_closure, pk.data(), sizeof(uint32_t) * CP_WORDS, cudaMemcpyHostToDevice, h->stream),
            "copy closure");
     FPC_CK(h, cudaStreamSynchronize(h->stream), "closure sync");
     h->have_closure = true;

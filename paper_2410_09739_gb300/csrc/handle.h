@@ -81,6 +81,10 @@ struct fpclbm {
     // parameters (Appendix D Step 3 numbering)
     double omega[27];
     double F[3] = {0, 0, 0};
+    double lid[2] = {0, 0};  // x and z velocity of the wall y = ny - 1/2
+    double smag[3] = {0, 0, 0};  // Smagorinsky C_s, u*, A+
+    void* d_smag = nullptr;      // (C_s D(y))^2 per row, storage of the arithmetic type
+    bool smag_dirty = true;
     int diffusion = FPCLBM_DIFF_FP;
     // launch configuration (autotuned) and graph cache
     int block = 256;

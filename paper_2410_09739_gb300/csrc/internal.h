@@ -16,9 +16,9 @@ struct StepLaunch {
 };
 
 // One time step of a single box.  odd selects the AA-pattern parity (0: own
-// slots, 1: neighbour slots), walls the y-wall bounce-back, force the source
+// slots, 1: neighbour slots), bc the boundary kind (BC_*), force the source
 // terms, mode MODE_FP / MODE_EQ / MODE_LEARNED.
-cudaError_t launch_step(int precision, int odd, int walls, int force, int mode, const StepArgs<double>& a64,
+cudaError_t launch_step(int precision, int odd, int bc, int force, int mode, const StepArgs<double>& a64,
                         const StepArgs<float>& a32, const StepLaunch& cfg, cudaStream_t st);
 
 // Auxiliary kernels (aux_kernels.cu).  All fields double.
@@ -27,7 +27,8 @@ struct BoxGeom {
     unsigned stride;
     unsigned ncells;
     int nx, ny, nz;
-    int walls;
+    int walls;  // 0: periodic, 1: bounce-back walls at y = -1/2, ny - 1/2, 2: on all six faces,
+                // 3: half channel (wall at y = -1/2, specular symmetry plane at y = ny - 1/2)
     FastDiv div_nx, div_nxny;
 };
 

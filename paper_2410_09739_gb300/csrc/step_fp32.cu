@@ -3,10 +3,10 @@
 
 namespace fpc {
 
-cudaError_t launch_step_fp32(int odd, int walls, int force, int mode, const StepArgs<float>& a, const StepLaunch& cfg,
+cudaError_t launch_step_fp32(int odd, int bc, int force, int mode, const StepArgs<float>& a, const StepLaunch& cfg,
                           cudaStream_t st)
 {
-    return step_dispatch<float, float>(odd, walls, force, mode, a, cfg, st);
+    return step_dispatch<float, float>(odd, bc, force, mode, a, cfg, st);
 }
 
 }  // namespace fpc

@@ -3,10 +3,10 @@
 
 namespace fpc {
 
-cudaError_t launch_step_fp64(int odd, int walls, int force, int mode, const StepArgs<double>& a, const StepLaunch& cfg,
+cudaError_t launch_step_fp64(int odd, int bc, int force, int mode, const StepArgs<double>& a, const StepLaunch& cfg,
                           cudaStream_t st)
 {
-    return step_dispatch<double, double>(odd, walls, force, mode, a, cfg, st);
+    return step_dispatch<double, double>(odd, bc, force, mode, a, cfg, st);
 }
 
 }  // namespace fpc

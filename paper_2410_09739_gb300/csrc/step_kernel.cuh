@@ -2,18 +2,24 @@
 // see cell.cuh): one thread per cell, one launch per time step.  MINB is the
 // minimum resident blocks per SM handed to __launch_bounds__, i.e. the
 // register cap (2: ~120, 3: ~80, 4: 64 registers); the autotuner times the
-// variants and keeps the fastest.
+// variants and keeps the fastest.  BC is one of the BC_* boundary kinds.
 #pragma once
 #include "cell.cuh"
 #include "internal.h"
 
 namespace fpc {
 
-template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_step(const StepArgs<R> a)
 {
-    const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= a.ncells) return;
+    unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = true;
+    if (cell >= a.ncells) {
+        // the learned closure is warp-collective: tail lanes stay, on a valid cell, without writing
+        if (MODE != MODE_LEARNED) return;
+        active = false;
+        cell = a.ncells - 1;
+    }
     CellGeom G;
     G.stride = a.stride;
     G.nx = a.nx;
@@ -22,8 +28,9 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepArgs<R> a)
     G.div_nx = a.div_nx;
     G.div_nxny = a.div_nxny;
     const Rates<R>& rt = a.rates;
-    update_cell<S, R, ODD, WALLS, FORCE, MODE>(static_cast<S*>(a.buf), G, cell, rt, a.Fx, a.Fy, a.Fz, rt.om[4],
-                                               rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.closure, a.flag);
+    update_cell<S, R, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, cell, rt, a.Fx, a.Fy, a.Fz, rt.om[4],
+                                            rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.closure, a.flag, active,
+                                            a.lid6x, a.lid6z, a.smag);
 }
 
 // ---------------------------------------------------------------------------
@@ -49,10 +56,12 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_step_pipe(const StepArgs<R> a, unsigned ntiles)
 {
     static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async moves 4, 8 or 16 bytes");
+    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y, "periodic or channel boxes only");
+    static_assert(MODE == MODE_FP || MODE == MODE_EQ, "FP and MCM modes only");
     extern __shared__ __align__(16) unsigned char fpc_smem[];
     S* sm = reinterpret_cast<S*>(fpc_smem);
     const unsigned T = blockDim.x, tid = threadIdx.x;
@@ -71,11 +80,11 @@ __global__ void __launch_bounds__(128, MINB) k_step_pipe(const StepArgs<R> a, un
         const unsigned cell = tile * T + tid;
         if (tile < ntiles && cell < a.ncells) {
             Nbr n;
-            if (ODD) n = make_nbr<WALLS>(G, cell);
+            if (ODD) n = make_nbr<BC>(G, cell);
             S* dst = sm + (size_t)stage * 27 * T + tid;
 #pragma unroll
             for (int s = 0; s < 27; ++s)
-                cp_async<sizeof(S)>(dst + s * T, load_ptr<S, ODD, WALLS>(buf, s, n, stride, cell));
+                cp_async<sizeof(S)>(dst + s * T, load_ptr<S, ODD, BC>(buf, s, n, stride, cell));
         }
         cp_async_commit();
     };
@@ -96,21 +105,21 @@ __global__ void __launch_bounds__(128, MINB) k_step_pipe(const StepArgs<R> a, un
                                                          rt.om[8], rt.om[9], a.closure);
             if (!ok) atomicOr(a.flag, 1);
             Nbr n;
-            if (ODD) n = make_nbr<WALLS>(G, cell);
+            if (ODD) n = make_nbr<BC>(G, cell);
 #pragma unroll
-            for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, WALLS>(buf, s, n, stride, cell), g[s]);
+            for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, cell), g[s]);
         }
         stage ^= 1;
     }
     cp_async_wait<0>();
 }
 
-template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
 {
     constexpr int T = 128;
     const size_t smem = 2ull * 27 * T * sizeof(S);
-    auto kern = k_step_pipe<S, R, ODD, WALLS, FORCE, MODE, 2 * MINB>;
+    auto kern = k_step_pipe<S, R, ODD, BC, FORCE, MODE, 2 * MINB>;
     static int per_sm = 0, sms = 0;  // benign race: every thread computes the same values
     if (per_sm == 0) {
         int dev = 0;
@@ -128,58 +137,83 @@ cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE, int MINB>
+template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
-    if constexpr (sizeof(S) >= 4) {
-        if (cfg.pipe) return step_go_pipe<S, R, ODD, WALLS, FORCE, MODE, MINB>(a, st);
+    // the pipelined variant retires tail lanes early, so it never runs the warp-collective
+    // learned mode; it exists for the FP and MCM modes of periodic and channel boxes
+    if constexpr (sizeof(S) >= 4 && (MODE == MODE_FP || MODE == MODE_EQ) && BC <= BC_WALLS_Y) {
+        if (cfg.pipe) return step_go_pipe<S, R, ODD, BC, FORCE, MODE, MINB>(a, st);
     }
     const int block = cfg.block > 0 ? cfg.block : 256;
     const unsigned grid = (a.ncells + block - 1) / block;
-    k_step<S, R, ODD, WALLS, FORCE, MODE, MINB><<<grid, block, 0, st>>>(a);
+    k_step<S, R, ODD, BC, FORCE, MODE, MINB><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-// Register-cap variants exist for the fp32-arithmetic FP and EQ modes; fp64
-// and the learned mode have one variant each.
-template <typename S, typename R, bool ODD, bool WALLS, bool FORCE, int MODE>
+// Register-cap variants exist for the fp32-arithmetic modes on boxes with
+// resting walls: 2, 3, 4 for FP and EQ; 1 (no cap) and 2 (128 registers) for
+// the learned mode, whose tensor-core MLP keeps the cell's state live.  fp64,
+// the Smagorinsky mode and moving walls have one variant each.
+template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE>
 cudaError_t step_by_minb(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
-    constexpr bool tunable = sizeof(R) == 4 && MODE != MODE_LEARNED;
-    if constexpr (tunable) {
-        if (cfg.minb == 3) return step_go<S, R, ODD, WALLS, FORCE, MODE, 3>(a, cfg, st);
-        if (cfg.minb == 4) return step_go<S, R, ODD, WALLS, FORCE, MODE, 4>(a, cfg, st);
-        return step_go<S, R, ODD, WALLS, FORCE, MODE, 2>(a, cfg, st);
+    constexpr bool fp32_fixed = sizeof(R) == 4 && bc_fixed(BC) && MODE != MODE_SMAG;
+    if constexpr (fp32_fixed && MODE != MODE_LEARNED) {
+        if (cfg.minb == 3) return step_go<S, R, ODD, BC, FORCE, MODE, 3>(a, cfg, st);
+        if (cfg.minb == 4) return step_go<S, R, ODD, BC, FORCE, MODE, 4>(a, cfg, st);
+        return step_go<S, R, ODD, BC, FORCE, MODE, 2>(a, cfg, st);
+    } else if constexpr (fp32_fixed) {
+        if (cfg.minb == 2) return step_go<S, R, ODD, BC, FORCE, MODE, 2>(a, cfg, st);
+        return step_go<S, R, ODD, BC, FORCE, MODE, 1>(a, cfg, st);
     } else {
-        return step_go<S, R, ODD, WALLS, FORCE, MODE, 1>(a, cfg, st);
+        return step_go<S, R, ODD, BC, FORCE, MODE, 1>(a, cfg, st);
     }
 }
 
-template <typename S, typename R, bool ODD, bool WALLS, bool FORCE>
+template <typename S, typename R, bool ODD, int BC, bool FORCE>
 cudaError_t step_by_mode(int mode, const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
     switch (mode) {
-        case MODE_FP: return step_by_minb<S, R, ODD, WALLS, FORCE, MODE_FP>(a, cfg, st);
-        case MODE_EQ: return step_by_minb<S, R, ODD, WALLS, FORCE, MODE_EQ>(a, cfg, st);
-        case MODE_LEARNED: return step_by_minb<S, R, ODD, WALLS, FORCE, MODE_LEARNED>(a, cfg, st);
+        case MODE_FP: return step_by_minb<S, R, ODD, BC, FORCE, MODE_FP>(a, cfg, st);
+        case MODE_EQ: return step_by_minb<S, R, ODD, BC, FORCE, MODE_EQ>(a, cfg, st);
+        case MODE_LEARNED:  // periodic and channel boxes (the closure's training data come from them)
+            if constexpr (BC == BC_PERIODIC || BC == BC_WALLS_Y)
+                return step_by_minb<S, R, ODD, BC, FORCE, MODE_LEARNED>(a, cfg, st);
+            break;
+        case MODE_SMAG:  // resting walls
+            if constexpr (bc_fixed(BC)) return step_by_minb<S, R, ODD, BC, FORCE, MODE_SMAG>(a, cfg, st);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename S, typename R, bool ODD, int BC>
+cudaError_t step_by_force(int force, int mode, const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
+{
+    return force ? step_by_mode<S, R, ODD, BC, true>(mode, a, cfg, st)
+                 : step_by_mode<S, R, ODD, BC, false>(mode, a, cfg, st);
+}
+
+template <typename S, typename R, bool ODD>
+cudaError_t step_by_bc(int bc, int force, int mode, const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
+{
+    switch (bc) {
+        case BC_PERIODIC: return step_by_force<S, R, ODD, BC_PERIODIC>(force, mode, a, cfg, st);
+        case BC_WALLS_Y: return step_by_force<S, R, ODD, BC_WALLS_Y>(force, mode, a, cfg, st);
+        case BC_WALLS_Y_LID: return step_by_force<S, R, ODD, BC_WALLS_Y_LID>(force, mode, a, cfg, st);
+        case BC_BOX_LID: return step_by_force<S, R, ODD, BC_BOX_LID>(force, mode, a, cfg, st);
+        case BC_HALF_CHANNEL: return step_by_force<S, R, ODD, BC_HALF_CHANNEL>(force, mode, a, cfg, st);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename S, typename R>
-cudaError_t step_dispatch(int odd, int walls, int force, int mode, const StepArgs<R>& a, const StepLaunch& cfg,
+cudaError_t step_dispatch(int odd, int bc, int force, int mode, const StepArgs<R>& a, const StepLaunch& cfg,
                           cudaStream_t st)
 {
-    if (odd) {
-        if (walls) return force ? step_by_mode<S, R, true, true, true>(mode, a, cfg, st)
-                                : step_by_mode<S, R, true, true, false>(mode, a, cfg, st);
-        return force ? step_by_mode<S, R, true, false, true>(mode, a, cfg, st)
-                     : step_by_mode<S, R, true, false, false>(mode, a, cfg, st);
-    }
-    if (walls) return force ? step_by_mode<S, R, false, true, true>(mode, a, cfg, st)
-                            : step_by_mode<S, R, false, true, false>(mode, a, cfg, st);
-    return force ? step_by_mode<S, R, false, false, true>(mode, a, cfg, st)
-                 : step_by_mode<S, R, false, false, false>(mode, a, cfg, st);
+    return odd ? step_by_bc<S, R, true>(bc, force, mode, a, cfg, st)
+               : step_by_bc<S, R, false>(bc, force, mode, a, cfg, st);
 }
 
 }  // namespace fpc

@@ -9,14 +9,14 @@ cudaError_t launch_step_fp32(int, int, int, int, const StepArgs<float>&, const S
 cudaError_t launch_step_fp16(int, int, int, int, const StepArgs<float>&, const StepLaunch&, cudaStream_t);
 cudaError_t launch_step_bf16(int, int, int, int, const StepArgs<float>&, const StepLaunch&, cudaStream_t);
 
-cudaError_t launch_step(int precision, int odd, int walls, int force, int mode, const StepArgs<double>& a64,
+cudaError_t launch_step(int precision, int odd, int bc, int force, int mode, const StepArgs<double>& a64,
                         const StepArgs<float>& a32, const StepLaunch& cfg, cudaStream_t st)
 {
     switch (precision) {
-        case P_FP64: return launch_step_fp64(odd, walls, force, mode, a64, cfg, st);
-        case P_FP32: return launch_step_fp32(odd, walls, force, mode, a32, cfg, st);
-        case P_FP16: return launch_step_fp16(odd, walls, force, mode, a32, cfg, st);
-        case P_BF16: return launch_step_bf16(odd, walls, force, mode, a32, cfg, st);
+        case P_FP64: return launch_step_fp64(odd, bc, force, mode, a64, cfg, st);
+        case P_FP32: return launch_step_fp32(odd, bc, force, mode, a32, cfg, st);
+        case P_FP16: return launch_step_fp16(odd, bc, force, mode, a32, cfg, st);
+        case P_BF16: return launch_step_bf16(odd, bc, force, mode, a32, cfg, st);
     }
     return cudaErrorInvalidValue;
 }

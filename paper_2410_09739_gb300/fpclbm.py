@@ -36,19 +36,25 @@ FPCLBM_FP32_STORE_BF16 = 3
 
 FPCLBM_BC_PERIODIC = 0
 FPCLBM_BC_WALLS_Y = 1
+FPCLBM_BC_BOX = 2
+FPCLBM_BC_HALF_CHANNEL = 3
 
 FPCLBM_DIFF_FP = 0
 FPCLBM_DIFF_EQUILIBRIUM = 1
 FPCLBM_DIFF_FP_LEARNED = 2
+FPCLBM_DIFF_FP_SMAGORINSKY = 3
 
 PRECISIONS = {"fp64": FPCLBM_FP64, "fp32": FPCLBM_FP32, "fp16": FPCLBM_FP32_STORE_FP16,
               "bf16": FPCLBM_FP32_STORE_BF16}
 
 EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fpclbm_set_params",
-            "fpclbm_set_rates", "fpclbm_set_force", "fpclbm_step", "fpclbm_moments", "fpclbm_diagnostics",
+            "fpclbm_set_rates", "fpclbm_set_force", "fpclbm_set_wall_velocity", "fpclbm_set_smagorinsky", "fpclbm_step", "fpclbm_moments", "fpclbm_diagnostics",
             "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_set_closure",
             "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc", "fpclbm_closure_sample",
-            "fpclbm_closure_train", "fpclbm_closure_grad")
+            "fpclbm_closure_train", "fpclbm_closure_grad",
+            "fpclbm2d_create", "fpclbm2d_init_fields", "fpclbm2d_set_params", "fpclbm2d_set_rates",
+            "fpclbm2d_set_force", "fpclbm2d_step", "fpclbm2d_moments", "fpclbm2d_get_populations",
+            "fpclbm2d_set_populations", "fpclbm2d_destroy", "fpclbm2d_last_error")
 
 
 class FpclbmError(RuntimeError):
@@ -78,6 +84,8 @@ def load(path: str = LIB_PATH):
     L.fpclbm_set_params.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.fpclbm_set_rates.argtypes = [_P, _D]
     L.fpclbm_set_force.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.fpclbm_set_wall_velocity.argtypes = [_P, ctypes.c_double, ctypes.c_double]
+    L.fpclbm_set_smagorinsky.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.fpclbm_step.argtypes = [_P, ctypes.c_longlong]
     L.fpclbm_moments.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int]
     L.fpclbm_diagnostics.argtypes = [_P, _D]
@@ -95,8 +103,20 @@ def load(path: str = LIB_PATH):
     L.fpclbm_destroy.argtypes = [_P]
     L.fpclbm_last_error.argtypes = [_P]
     L.fpclbm_last_error.restype = ctypes.c_char_p
+    L.fpclbm2d_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
+    L.fpclbm2d_init_fields.argtypes = [_P, _P, _P, _P, ctypes.c_int]
+    L.fpclbm2d_set_params.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.fpclbm2d_set_rates.argtypes = [_P, _D]
+    L.fpclbm2d_set_force.argtypes = [_P, ctypes.c_double, ctypes.c_double]
+    L.fpclbm2d_step.argtypes = [_P, ctypes.c_longlong]
+    L.fpclbm2d_moments.argtypes = [_P, _P, _P, _P, ctypes.c_int]
+    L.fpclbm2d_get_populations.argtypes = [_P, _P]
+    L.fpclbm2d_set_populations.argtypes = [_P, _P]
+    L.fpclbm2d_destroy.argtypes = [_P]
+    L.fpclbm2d_last_error.argtypes = [_P]
+    L.fpclbm2d_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name != "fpclbm_last_error":
+        if not name.endswith("last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -165,6 +185,14 @@ def fpclbm_set_rates(h, omega):
 
 def fpclbm_set_force(h, Fx: float, Fy: float, Fz: float):
     return _check(h, load().fpclbm_set_force(h, float(Fx), float(Fy), float(Fz)))
+
+
+def fpclbm_set_wall_velocity(h, ux: float, uz: float):
+    return _check(h, load().fpclbm_set_wall_velocity(h, float(ux), float(uz)))
+
+
+def fpclbm_set_smagorinsky(h, cs: float, u_star: float, a_plus: float):
+    return _check(h, load().fpclbm_set_smagorinsky(h, float(cs), float(u_star), float(a_plus)))
 
 
 def fpclbm_step(h, n: int):
@@ -328,6 +356,12 @@ class Lattice:
     def set_force(self, Fx, Fy=0.0, Fz=0.0):
         return fpclbm_set_force(self.h, Fx, Fy, Fz)
 
+    def set_wall_velocity(self, ux, uz=0.0):
+        return fpclbm_set_wall_velocity(self.h, ux, uz)
+
+    def set_smagorinsky(self, cs, u_star=0.0, a_plus=26.0):
+        return fpclbm_set_smagorinsky(self.h, cs, u_star, a_plus)
+
     def step(self, n: int = 1):
         return fpclbm_step(self.h, n)
 
@@ -357,3 +391,120 @@ class Lattice:
 
     def set_closure(self, bf16_bits):
         return fpclbm_set_closure(self.h, bf16_bits)
+
+
+# --- the 2D (D2Q9) handle -----------------------------------------------------------------
+
+def _check2(h, rc: int):
+    if rc != FPCLBM_OK:
+        msg = load().fpclbm2d_last_error(h)
+        raise FpclbmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def fpclbm2d_create(nx: int, ny: int, precision: int, stream: int = 0):
+    h = _P()
+    _check2(None, load().fpclbm2d_create(ctypes.byref(h), nx, ny, precision, _P(stream) if stream else None))
+    return h
+
+
+def fpclbm2d_init_fields(h, rho, ux, uy, on_device: int = 0):
+    return _check2(h, load().fpclbm2d_init_fields(h, *(_ptr(a, on_device) for a in (rho, ux, uy)), int(on_device)))
+
+
+def fpclbm2d_set_params(h, tau: float, bulk_rate: float = 0.0, drift: float = 0.0, diffusion: int = FPCLBM_DIFF_FP):
+    return _check2(h, load().fpclbm2d_set_params(h, float(tau), float(bulk_rate), float(drift), int(diffusion)))
+
+
+def fpclbm2d_set_rates(h, omega):
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    assert om.size == 9
+    return _check2(h, load().fpclbm2d_set_rates(h, om.ctypes.data_as(_D)))
+
+
+def fpclbm2d_set_force(h, Fx: float, Fy: float):
+    return _check2(h, load().fpclbm2d_set_force(h, float(Fx), float(Fy)))
+
+
+def fpclbm2d_step(h, n: int):
+    return _check2(h, load().fpclbm2d_step(h, int(n)))
+
+
+def fpclbm2d_moments(h, rho, ux, uy, on_device: int = 0):
+    return _check2(h, load().fpclbm2d_moments(h, *(_ptr(a, on_device) for a in (rho, ux, uy)), int(on_device)))
+
+
+def fpclbm2d_get_populations(h, f):
+    return _check2(h, load().fpclbm2d_get_populations(h, _ptr(f, 0)))
+
+
+def fpclbm2d_set_populations(h, f):
+    return _check2(h, load().fpclbm2d_set_populations(h, _ptr(f, 0)))
+
+
+def fpclbm2d_destroy(h):
+    return load().fpclbm2d_destroy(h)
+
+
+def fpclbm2d_last_error(h) -> str:
+    m = load().fpclbm2d_last_error(h)
+    return m.decode() if m else ""
+
+
+class Lattice2D:
+    """One periodic D2Q9 box; methods map 1:1 onto the fpclbm2d_* calls.  Arrays are [ny, nx]."""
+
+    def __init__(self, nx: int, ny: int, precision="fp32", stream: int = 0):
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.shape = (ny, nx)
+        self.ncells = nx * ny
+        self.h = fpclbm2d_create(nx, ny, self.precision, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            fpclbm2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _f64(a):
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+
+    def init_fields(self, rho, ux, uy):
+        return fpclbm2d_init_fields(self.h, *(self._f64(a) for a in (rho, ux, uy)))
+
+    def set_params(self, tau, bulk_rate=0.0, drift=0.0, diffusion=FPCLBM_DIFF_FP):
+        return fpclbm2d_set_params(self.h, tau, bulk_rate, drift, diffusion)
+
+    def set_rates(self, omega):
+        return fpclbm2d_set_rates(self.h, omega)
+
+    def set_force(self, Fx, Fy=0.0):
+        return fpclbm2d_set_force(self.h, Fx, Fy)
+
+    def step(self, n: int = 1):
+        return fpclbm2d_step(self.h, n)
+
+    def moments(self):
+        outs = [np.empty(self.ncells) for _ in range(3)]
+        fpclbm2d_moments(self.h, *outs)
+        return tuple(o.reshape(self.shape) for o in outs)
+
+    def get_populations(self):
+        f = np.empty((9, self.ncells))
+        fpclbm2d_get_populations(self.h, f)
+        return f.reshape((9,) + self.shape)
+
+    def set_populations(self, f):
+        return fpclbm2d_set_populations(self.h, self._f64(f))

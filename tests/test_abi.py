@@ -11,7 +11,7 @@ HEADER = os.path.join(ROOT, "include", "fpclbm.h")
 
 def declared_symbols():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"FPCLBM_API\s+[\w\s\*]+?\b(fpclbm_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"FPCLBM_API\s+[\w\s\*]+?\b(fpclbm(?:2d)?_\w+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")

@@ -4,9 +4,10 @@ Tolerances: sampled features/labels are fp64 on the device and rounded to
 float32 on output (relative 2^-24, checked at 1e-5 of each column's scale);
 gradients of the bf16-weight fp32 kernels against the fp64 oracle with the
 same bf16 weights: relative 2-norm per tensor <= 2e-2 (the stated bound;
-fp32 summation of ~64-term sums gives ~1e-6); inference: the learned shear
-rate perturbs the collision at fp32 level, so one step is checked at 1e-6
-absolute like every fp32 path.
+fp32 summation of ~64-term sums gives ~1e-6); inference (tensor-core MLP with
+bf16 operands): the oracle-side network takes the same bf16 roundings of its
+inputs and first hidden layer, and one step is checked at 1e-6 absolute like
+every fp32 path.
 """
 import numpy as np
 import pytest
@@ -90,8 +91,18 @@ def test_training_fits_a_smooth_target():
     assert np.sqrt(np.mean((y - t) ** 2)) < 0.25 * np.std(t)
 
 
+def _mlp_bf16_operands(theta, x):
+    """The inference arithmetic of the fused kernel: bf16 operands (inputs and first hidden layer),
+    products accumulated exactly here (fp32 on the GPU), tanh exact here (MUFU on the GPU)."""
+    p = C.unpack(theta)
+    xb, _ = bf16_round(x)
+    h1, _ = bf16_round(np.tanh(p["W1"] @ xb + p["b1"]))
+    h2 = np.tanh(p["W2"] @ h1 + p["b2"])
+    return float(p["W3"][0] @ h2 + p["b3"][0])
+
+
 def _learned_step_oracle(f0, theta, omega_base, bc=0):
-    """One step of the learned-mode collision with the oracle: per cell, delta omega from the fp64 MLP
+    """One step of the learned-mode collision with the oracle: per cell, delta omega from the MLP
     on (kappa_2 - kappa_2^Mv, u), added to the shear rates (clamped to [0.02, 1.98]), then collide and
     push-stream."""
     _, nz, ny, nx = f0.shape
@@ -108,10 +119,10 @@ def _learned_step_oracle(f0, theta, omega_base, bc=0):
                 K = lambda s: k[mnp.index(s)]  # noqa: E731
                 feat = np.array([K((2, 0, 0)) - rho / 3, K((0, 2, 0)) - rho / 3, K((0, 0, 2)) - rho / 3,
                                  K((1, 1, 0)), K((1, 0, 1)), K((0, 1, 1)), u[0], u[1], u[2]])
-                dw, _ = C.forward(theta, feat[None, :])
+                dw = _mlp_bf16_operands(theta, feat)
                 om = omega_base.copy()
                 for j in (4, 5, 6, 8, 9):
-                    om[j] = min(max(om[j] + dw[0], 0.02), 1.98)
+                    om[j] = min(max(om[j] + dw, 0.02), 1.98)
                 ft = O.collide(f, (0, 0, 0), om, O.EQ_MODE_FP)
                 for a in range(27):
                     out[a, (z + e[a, 2]) % nz, (y + e[a, 1]) % ny, (x + e[a, 0]) % nx] = ft[a]
@@ -119,10 +130,15 @@ def _learned_step_oracle(f0, theta, omega_base, bc=0):
 
 
 def test_learned_inference_matches_oracle():
+    """60 cells: one full warp and a ragged tail warp.  Network with the output scale of a trained
+    closure (|delta omega| ~ 5e-2).  Both sides round the inputs and the first hidden layer to bf16;
+    what remains is the MUFU tanh (absolute ~2^-11 per activation): |d delta omega| <~ 64 * 0.05 *
+    5e-4 = 1.6e-3 at worst, and one step moves by ~9e-8 per 1e-4 of delta omega here, so <= 1e-6
+    holds with margin while the closure itself moves the step by ~5e-5."""
     nx, ny, nz = 5, 4, 3
     rng = np.random.default_rng(9)
-    th = C.init_params(3) * 20.0
-    th[-65:-1] = rng.uniform(-0.5, 0.5, 64)
+    th = C.init_params(3) * 3.0
+    th[-65:-1] = rng.uniform(-0.05, 0.05, 64)
     th[-1] = -0.05
     wv, wbits = bf16_round(th)
     rho, ux, uy, uz = W.random_fields(nx, ny, nz, seed=4, u_amp=0.05)
