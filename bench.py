@@ -97,7 +97,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-STEP_KERNEL_SOURCES = ("common.cuh", "collide.cuh", "closure.cuh", "cell.cuh", "step_kernel.cuh", "step_fp32.cu",
+STEP_KERNEL_SOURCES = ("common.cuh", "collide.cuh", "pair.cuh", "closure.cuh", "cell.cuh", "step_kernel.cuh", "step_fp32.cu",
                        "step_fp16.cu", "step_bf16.cu", "step_fp64.cu", "step_kernels.cu", "internal.h")
 
 
@@ -342,7 +342,8 @@ def main():
     cfg.update({"precision": prec, "storage": prec, "lbm_steps_per_bench_step": args.inner,
                 "l2": "inputs larger than L2 (%.2f GB populations)" % (27 * BYTES[prec] * ncell / 1e9),
                 "parallelism": "replicas" if world > 1 else "1 GPU"})
-    kname = "fpc::k_ens_step (persistent, AA even/odd)" if args.workload == "ensemble" else "fpc::k_step (AA even/odd)"
+    kname = ("fpc::k_ens_step (persistent, AA even/odd)" if args.workload == "ensemble" else
+             "fpc::k_step / fpc::k_step_pair (AA even/odd, the autotuner's variant)")
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,

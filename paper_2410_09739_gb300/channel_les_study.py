@@ -3,7 +3,10 @@ on a half channel closed by a specular symmetry plane, driven by F_x = u*^2 / H.
 
 Domain 2 pi H x H x pi H (x, y wall-normal, z), wall at y = -1/2, symmetry plane at y = H - 1/2,
 Re* = u* H / nu.  Initial state: the lower half of a laminar channel of height 2H with bulk
-velocity 16 u* plus seeded +-10 % perturbations.  After --spinup friction times T* = H / u*,
+velocity 16 u* plus seeded +-10 % perturbations and (--vortices A) large-scale streaks and
+streamwise vortices of amplitude A u* (spanwise wavenumber 4, streamwise 2; the wall-normal
+shapes vanish at the wall and respect the symmetry plane), which let the flow transition within
+a few friction times instead of relaminarising.  After --spinup friction times T* = H / u*,
 statistics over --collect T* (every --every steps; averages over x, z and time):
 mean U(y), rms fluctuations, Reynolds shear stress -<u'v'>, all in wall units with the nominal u*.
 
@@ -41,13 +44,28 @@ def parse(argv=None):
     p.add_argument("--u-star", type=float, default=0.006)
     p.add_argument("--cs", type=float, default=0.1, help="Smagorinsky constant")
     p.add_argument("--a-plus", type=float, default=26.0, help="van Driest constant")
-    p.add_argument("--spinup", type=float, default=30.0, help="friction times before statistics")
+    p.add_argument("--spinup", type=float, default=40.0, help="friction times before statistics")
     p.add_argument("--collect", type=float, default=20.0, help="friction times of statistics")
     p.add_argument("--every", type=int, default=200, help="steps between samples")
     p.add_argument("--precision", default="fp32")
     p.add_argument("--model", default="smagorinsky", choices=["smagorinsky", "none"])
+    p.add_argument("--vortices", type=float, default=4.0, help="streak/vortex amplitude in units of u*")
     p.add_argument("--seed", type=int, default=7)
     return p.parse_args(argv)
+
+
+def perturbation(nx, ny, nz, H, amp):
+    """Streaks u' ~ sin(pi y / 2H) cos(k_z z) and vortices v' ~ sin(pi y / H) sin(k_z z) cos(k_x x),
+    w' ~ cos(pi y / H) cos(k_z z) sin(k_x x): zero u', v' at the wall, zero v' and du'/dy at the
+    symmetry plane."""
+    x = 2 * math.pi * np.arange(nx) / nx
+    z = 2 * math.pi * np.arange(nz) / nz
+    y = (np.arange(ny) + 0.5) / H
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    du = amp * np.sin(0.5 * math.pi * Y) * np.cos(4 * Z)
+    dv = 0.5 * amp * np.sin(math.pi * Y) * np.sin(4 * Z) * np.cos(2 * X)
+    dw = 0.5 * amp * np.cos(math.pi * Y) * (1 - np.exp(-8 * Y)) * np.cos(4 * Z) * np.sin(2 * X)
+    return du, dv, dw
 
 
 def run(args):
@@ -68,8 +86,12 @@ def run(args):
     else:
         lat.set_params(tau)
     lat.set_force(Fx, 0.0, 0.0)
-    rho, ux, uy, uz = W.channel_fields(nx, 2 * ny, nz, us, seed=args.seed)
-    lat.init_fields(*(np.ascontiguousarray(a[:, :ny, :]) for a in (rho, ux, uy, uz)))
+    rho, ux, uy, uz = (np.ascontiguousarray(a[:, :ny, :]) for a in W.channel_fields(nx, 2 * ny, nz, us,
+                                                                                       seed=args.seed))
+    if args.vortices > 0:
+        du, dv, dw = perturbation(nx, ny, nz, H, args.vortices * us)
+        ux, uy, uz = ux + du, uy + dv, uz + dw
+    lat.init_fields(rho, ux, uy, uz)
 
     t0 = time.perf_counter()
     n_spin = int(round(args.spinup * Tstar))
@@ -126,7 +148,8 @@ def run(args):
         "config": {"domain": [nx, ny, nz], "H": H, "re_tau": args.re_tau, "u_star": us, "nu": nu, "tau": tau,
                    "Fx": Fx, "Cs": args.cs if args.model == "smagorinsky" else 0.0, "A_plus": args.a_plus,
                    "friction_time_steps": Tstar, "spinup_T": args.spinup, "collect_T": args.collect,
-                   "samples": samples, "precision": args.precision, "model": args.model},
+                   "samples": samples, "precision": args.precision, "model": args.model,
+                   "vortices_over_u_star": args.vortices},
         "bulk_velocity_over_u_star": float(np.mean(U) / us),
         "centreline_u_plus": float(uplus[-1]),
         "viscous_sublayer_max_abs_dev_u_plus": float(np.nanmax(np.abs(uplus[visc] - law[visc]))) if visc.any() else None,

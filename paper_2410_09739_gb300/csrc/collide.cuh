@@ -27,6 +27,7 @@
 // lower moments; kappa^Mv_122 carries Pi_110 Pi_012 (continuous form).
 #pragma once
 #include "common.cuh"
+#include "pair.cuh"
 
 namespace fpc {
 

@@ -340,14 +340,17 @@ void save_tune_file()
     std::fclose(fp);
 }
 
-// FPCLBM_LAUNCH = "block:minb:pipe" forces a single-box launch configuration.
+// FPCLBM_LAUNCH = "block:minb:variant" forces a single-box launch configuration
+// (variant 0: one cell per thread, 1: cp.async-pipelined, 2: two cells per thread).
 bool forced_launch(TuneChoice& c)
 {
     const char* v = std::getenv("FPCLBM_LAUNCH");
     if (!v || !v[0]) return false;
     int b = 0, m = 0, p = 0;
-    if (std::sscanf(v, "%d:%d:%d", &b, &m, &p) != 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4) return false;
-    c = {b, m, 0, p ? 1 : 0};
+    if (std::sscanf(v, "%d:%d:%d", &b, &m, &p) != 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4 || p < 0 ||
+        p > 2)
+        return false;
+    c = {b, m, 0, p};
     return true;
 }
 
@@ -370,6 +373,8 @@ int autotune(fpclbm* h)
     const bool fp32_math = h->precision != FPCLBM_FP64 && (md == MODE_FP || md == MODE_EQ) && fixed_walls;
     const bool pipe_ok = elem_size(h->precision) >= 4 && (md == MODE_FP || md == MODE_EQ) &&
                          (kb == BC_PERIODIC || kb == BC_WALLS_Y);
+    // paired variant (two cells per thread, packed fp32): fp32 arithmetic, periodic and channel
+    const bool pair_ok = fp32_math && (kb == BC_PERIODIC || kb == BC_WALLS_Y);
     if (h->ensemble) {
         for (int minb : {2, 3})
             for (int block : {128, 256}) {
@@ -381,6 +386,7 @@ int autotune(fpclbm* h)
             for (int block : {128, 256}) cands.push_back({block, minb, 0, 0});
         if (pipe_ok)
             for (int minb : {2, 3, 4}) cands.push_back({128, minb, 0, 1});
+        if (pair_ok) cands.push_back({128, 2, 0, 2});  // 4 blocks of 128 threads, 128 registers
     } else if (mode_of(h) == MODE_LEARNED && h->precision != FPCLBM_FP64 && fixed_walls) {
         // capped at 128 registers first: twice the resident warps of the uncapped variant
         for (int minb : {2, 1})
@@ -391,7 +397,8 @@ int autotune(fpclbm* h)
     }
     TuneChoice forced;
     if (!h->ensemble && forced_launch(forced)) {
-        if (forced.pipe && !pipe_ok) forced.pipe = 0;
+        if ((forced.pipe == 1 && !pipe_ok) || (forced.pipe == 2 && !pair_ok)) forced.pipe = 0;
+        if (forced.pipe == 2) forced.minb = 2;
         if (!fp32_math && mode_of(h) != MODE_LEARNED) forced.minb = 1;  // learned: 1 or 2 (else 1)
         h->block = forced.block;
         h->minb = forced.minb;

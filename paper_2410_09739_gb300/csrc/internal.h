@@ -12,7 +12,8 @@ enum { P_FP64 = 0, P_FP32 = 1, P_FP16 = 2, P_BF16 = 3 };
 struct StepLaunch {
     int block;     // threads per block (<= 256)
     int minb = 2;  // register-cap variant: minimum resident blocks of 256 threads per SM (2, 3 or 4)
-    int pipe = 0;  // 1: software-pipelined persistent variant (cp.async prefetch), 4/8-byte storage only
+    int pipe = 0;  // 1: software-pipelined persistent variant (cp.async prefetch), 4/8-byte storage only;
+                   // 2: paired variant (two cells per thread on the packed fp32 pipe)
 };
 
 // One time step of a single box.  odd selects the AA-pattern parity (0: own

@@ -137,13 +137,104 @@ cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Paired variant: each thread updates cells c and c + half with the packed
+// fp32 arithmetic of pair.cuh (one instruction per operation for both cells).
+// Loads and stores stay per cell, so a warp's accesses are as coalesced as
+// in k_step; each cell still reads and writes only its own AA addresses.
+// ---------------------------------------------------------------------------
+
+template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, unsigned half)
+{
+    unsigned c1 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c1 >= half) return;
+    const bool two = c1 + half < a.ncells;
+    CellGeom G;
+    G.stride = a.stride;
+    G.nx = a.nx;
+    G.ny = a.ny;
+    G.nz = a.nz;
+    G.div_nx = a.div_nx;
+    G.div_nxny = a.div_nxny;
+    S* __restrict__ buf = static_cast<S*>(a.buf);
+    const unsigned stride = a.stride;
+    f2 g[27];
+    {
+        Nbr n;
+        if (ODD) n = make_nbr<BC>(G, c1);
+#pragma unroll
+        for (int s = 0; s < 27; ++s) g[s].v.x = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, c1));
+        const unsigned c2 = two ? c1 + half : c1;
+        if (ODD) n = make_nbr<BC>(G, c2);
+#pragma unroll
+        for (int s = 0; s < 27; ++s) g[s].v.y = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, c2));
+    }
+    const Rates<f2>& rt = a.rates;
+    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, a.Fx, a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6], rt.om[8],
+                                                  rt.om[9], nullptr);
+    if (!ok) atomicOr(a.flag, 1);
+    asm volatile("" : "+r"(c1));  // rebuild the store addresses (see update_cell)
+    Nbr n;
+    if (ODD) n = make_nbr<BC>(G, c1);
+#pragma unroll
+    for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c1), g[s].v.x);
+    if (two) {
+        const unsigned c2 = c1 + half;
+        if (ODD) n = make_nbr<BC>(G, c2);
+#pragma unroll
+        for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c2), g[s].v.y);
+    }
+}
+
+// The launch arguments with every scalar duplicated into both lanes.
+inline StepArgs<f2> pair_args(const StepArgs<float>& a)
+{
+    StepArgs<f2> p;
+    p.buf = a.buf;
+    p.stride = a.stride;
+    p.ncells = a.ncells;
+    p.nx = a.nx;
+    p.ny = a.ny;
+    p.nz = a.nz;
+    p.div_nx = a.div_nx;
+    p.div_nxny = a.div_nxny;
+    p.Fx = f2(a.Fx, a.Fx);
+    p.Fy = f2(a.Fy, a.Fy);
+    p.Fz = f2(a.Fz, a.Fz);
+    p.lid6x = f2(a.lid6x, a.lid6x);
+    p.lid6z = f2(a.lid6z, a.lid6z);
+    for (int j = 0; j < 27; ++j) {
+        p.rates.om[j] = f2(a.rates.om[j], a.rates.om[j]);
+        p.rates.keep[j] = f2(a.rates.keep[j], a.rates.keep[j]);
+        p.rates.src[j] = f2(a.rates.src[j], a.rates.src[j]);
+    }
+    p.flag = a.flag;
+    p.closure = nullptr;
+    p.smag = nullptr;
+    return p;
+}
+
+template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB>
+cudaError_t step_go_pair(const StepArgs<float>& a, cudaStream_t st)
+{
+    const unsigned half = (a.ncells + 1) / 2;
+    k_step_pair<S, ODD, BC, FORCE, MODE, 2 * MINB><<<(half + 127) / 128, 128, 0, st>>>(pair_args(a), half);
+    return cudaGetLastError();
+}
+
 template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
+    // paired variant: fp32 arithmetic, FP and MCM modes, periodic and channel boxes, one register
+    // cap (4 blocks of 128 threads: 128 registers hold two cells without spilling)
+    if constexpr (sizeof(R) == 4 && (MODE == MODE_FP || MODE == MODE_EQ) && BC <= BC_WALLS_Y && MINB == 2) {
+        if (cfg.pipe == 2) return step_go_pair<S, ODD, BC, FORCE, MODE, MINB>(a, st);
+    }
     // the pipelined variant retires tail lanes early, so it never runs the warp-collective
     // learned mode; it exists for the FP and MCM modes of periodic and channel boxes
     if constexpr (sizeof(S) >= 4 && (MODE == MODE_FP || MODE == MODE_EQ) && BC <= BC_WALLS_Y) {
-        if (cfg.pipe) return step_go_pipe<S, R, ODD, BC, FORCE, MODE, MINB>(a, st);
+        if (cfg.pipe == 1) return step_go_pipe<S, R, ODD, BC, FORCE, MODE, MINB>(a, st);
     }
     const int block = cfg.block > 0 ? cfg.block : 256;
     const unsigned grid = (a.ncells + block - 1) / block;

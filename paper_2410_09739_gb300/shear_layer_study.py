@@ -9,9 +9,10 @@ L = 64, 128, 256 with the bulk rate omega_3 = 1, and Ma 0.05, 0.2, 0.3 with omeg
 
 The paper judges the cases by eye from vorticity plots (one rolled-up vortex per layer, or
 spurious secondary vortices).  This study reports numbers instead: whether the run stayed finite,
-the number of vorticity cores of each sign (local extrema of the vorticity beyond 30 % of its
-peak: 1 and 1 for a resolved roll-up), and the L2 distance of the vorticity field, sampled at
-t = 1 onto the 64 x 64 grid, from the finest FPC run of the same Mach number.
+the number of vortex blobs of each sign (connected regions, periodic, where the vorticity exceeds
+half of its peak magnitude: 1 and 1 for a clean roll-up of the two layers, more when secondary
+vortices form), and the L2 distance of the vorticity field, sampled at t = 1 onto the 64 x 64
+grid, from the finest FPC run of the same Mach number and bulk rate.
 
 Usage: python -m paper_2410_09739_gb300.shear_layer_study [--sizes 64 128 256] [--precision fp64]
 Prints one JSON object.
@@ -51,16 +52,31 @@ def vorticity(ux, uy, L, U):
     return (dvdx - dudy) * L / U
 
 
-def cores(om, frac=0.3):
-    """Local maxima of +om and of -om (8 neighbours, periodic) beyond frac of the peak |om|."""
+def blobs(mask):
+    """Connected regions (4-neighbour, periodic in both directions) of a boolean field."""
+    ny, nx = mask.shape
+    lab = np.zeros(mask.shape, dtype=np.int64)
+    n = 0
+    for j0, i0 in zip(*np.nonzero(mask)):
+        if lab[j0, i0]:
+            continue
+        n += 1
+        lab[j0, i0] = n
+        stack = [(j0, i0)]
+        while stack:
+            j, i = stack.pop()
+            for dj, di in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                jj, ii = (j + dj) % ny, (i + di) % nx
+                if mask[jj, ii] and not lab[jj, ii]:
+                    lab[jj, ii] = n
+                    stack.append((jj, ii))
+    return n
+
+
+def cores(om, frac=0.5):
+    """Vortex blobs of each sign: connected regions where +om (-om) exceeds frac of the peak |om|."""
     thr = frac * np.max(np.abs(om))
-    out = []
-    for s in (1, -1):
-        v = s * om
-        nb = np.max([np.roll(np.roll(v, dy, 0), dx, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
-                     if (dx, dy) != (0, 0)], axis=0)
-        out.append(int(np.sum((v > nb) & (v > thr))))
-    return out
+    return [blobs(om > thr), blobs(-om > thr)]
 
 
 def sample64(om, L):
