@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--inner", type=int, default=64, help="LBM steps per bench step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variants", action="store_true", help="also time fp16/bf16 storage")
-    p.add_argument("--workload", default="tgv", choices=["tgv", "channel", "cavity", "ensemble"])
+    p.add_argument("--workload", default="tgv", choices=["tgv", "channel", "cavity", "ensemble", "shear2d"])
     return p.parse_args()
 
 
@@ -198,6 +198,24 @@ def cpu_oracle_sample(n, tau, u0, target_s=15.0):
                 n, n, n, done, el)}
 
 
+def cpu_oracle_sample_2d(L, tau, U, target_s=15.0):
+    """The D2Q9 FP64 oracle on a 256 x 256 sample of the shear-layer workload (~target_s seconds)."""
+    from oracle import oracle2d as O2
+    import oracle as O
+    n = min(L, 256)
+    f = O2.init_equilibrium(*W.shear_layers(n, U))
+    om = O2.rates(tau)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        f = O2.step(f, omega=om)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            break
+    return {"value": n * n * done / el / 1e6, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
+            "sample": "%d x %d shear layers (D2Q9), %d FP64 oracle steps, %.1f s" % (n, n, done, el)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -270,6 +288,13 @@ def setup(args, F, prec, stream):
         one = np.ones((n, n, n))
         flds = (one, 0 * one, 0 * one, 0 * one)
         cfg = {"workload": "lid-driven cubic cavity 150^3, Re=1000, Ma=0.1, walls on all faces, tau=%.6f" % tau}
+    elif args.workload == "shear2d":
+        n, U = 4096, 0.2 / 3 ** 0.5
+        tau = 0.5 + 3 * U * n / 30000.0
+        lat = F.Lattice2D(n, n, prec, stream=stream)
+        lat.set_params(tau)
+        flds = W.shear_layers(n, U)
+        cfg = {"workload": "D2Q9 doubly periodic shear layers 4096^2, Re=30000, Ma=0.2, tau=%.6f" % tau}
     else:
         sides, taus = W.ensemble_config(256, seed=2410)
         dims = [(s_, s_, s_) for s_ in sides]
@@ -296,6 +321,8 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream().cuda_stream
     prec0 = args.precision if args.workload != "ensemble" else "fp32"
+    two_d = args.workload == "shear2d"
+    qb = 18 if two_d else 54  # algorithmic bytes per cell update in units of the storage size
     results = {}
     precs = [prec0] + ([p for p in ("fp16", "bf16") if p != prec0] if args.variants and args.workload != "ensemble"
                        else [])
@@ -314,19 +341,22 @@ def main():
         results[prec] = {"seconds": el, "clocks": ck}
         if prec == prec0:
             # e2e: host buffers through the C ABI, copies inside the timed region
-            hb = [torch.empty(ncell, dtype=torch.float64).pin_memory().numpy() for _ in range(8)]
-            for a, src in zip(hb[:4], flat):
+            nf = 3 if two_d else 4
+            hb = [torch.empty(ncell, dtype=torch.float64).pin_memory().numpy() for _ in range(2 * nf)]
+            for a, src in zip(hb[:nf], flat):
                 a[:] = src
+            init, mom = ((F.fpclbm2d_init_fields, F.fpclbm2d_moments) if two_d else
+                         (F.fpclbm_init_fields, F.fpclbm_moments))
             for _ in range(2):
-                F.fpclbm_init_fields(lat.h, *hb[:4], on_device=0)
+                init(lat.h, *hb[:nf], on_device=0)
                 lat.step(args.inner)
-                F.fpclbm_moments(lat.h, *hb[4:], on_device=0)
+                mom(lat.h, *hb[nf:], on_device=0)
             barrier(world)
             t0 = time.perf_counter()
             for _ in range(args.steps):
-                F.fpclbm_init_fields(lat.h, *hb[:4], on_device=0)
+                init(lat.h, *hb[:nf], on_device=0)
                 lat.step(args.inner)
-                F.fpclbm_moments(lat.h, *hb[4:], on_device=0)
+                mom(lat.h, *hb[nf:], on_device=0)
             results[prec]["e2e_s"] = max_over_ranks(time.perf_counter() - t0, world)
         lat.close()
     if rank != 0:
@@ -336,13 +366,14 @@ def main():
     value = ncell * args.inner * args.steps * world / el / 1e6
     launches = args.inner * args.steps
     per_launch = el / launches
-    alg_bytes = 54 * BYTES[prec] * ncell
+    alg_bytes = qb * BYTES[prec] * ncell
     peak, peak_kind = peaks()
     achieved = alg_bytes / per_launch / 1e9
     cfg.update({"precision": prec, "storage": prec, "lbm_steps_per_bench_step": args.inner,
                 "l2": "inputs larger than L2 (%.2f GB populations)" % (27 * BYTES[prec] * ncell / 1e9),
                 "parallelism": "replicas" if world > 1 else "1 GPU"})
     kname = ("fpc::k_ens_step (persistent, AA even/odd)" if args.workload == "ensemble" else
+             "fpc::k_step2d (D2Q9, AA even/odd)" if two_d else
              "fpc::k_step / fpc::k_step_pair (AA even/odd, the autotuner's variant)")
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -354,17 +385,22 @@ def main():
                      "traffic": ncu_traffic(prec, args.size) if args.workload == "tgv" else None,
                      "peak_source": peak_kind, "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": ncell * args.inner * args.steps * world / results[prec]["e2e_s"] / 1e6, "unit": "MLUPS",
-                "h2d_bytes_per_step": 4 * 8 * ncell, "d2h_bytes_per_step": 4 * 8 * ncell},
+                "h2d_bytes_per_step": (3 if two_d else 4) * 8 * ncell,
+                "d2h_bytes_per_step": (3 if two_d else 4) * 8 * ncell},
         "gpu_launches": launches,
         "clocks": results[prec]["clocks"],
     }
     if len(results) > 1:
         out["variants"] = {p: {"MLUPS": ncell * args.inner * args.steps * world / r["seconds"] / 1e6,
-                               "frac_hbm": 54 * BYTES[p] * ncell / (r["seconds"] / launches) / 1e9 / peak}
+                               "frac_hbm": qb * BYTES[p] * ncell / (r["seconds"] / launches) / 1e9 / peak}
                            for p, r in results.items()}
     if world == 1 and not args.no_cpu_baseline:
-        n, u0 = args.size, 0.05
-        out["cpu_baseline"] = cpu_oracle_sample(n, 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5, u0)
+        if two_d:
+            U = 0.2 / 3 ** 0.5
+            out["cpu_baseline"] = cpu_oracle_sample_2d(4096, 0.5 + 3 * U * 256 / 30000.0, U)
+        else:
+            n, u0 = args.size, 0.05
+            out["cpu_baseline"] = cpu_oracle_sample(n, 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5, u0)
     print(json.dumps(out), flush=True)
 
 

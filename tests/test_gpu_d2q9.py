@@ -37,7 +37,8 @@ def test_fp64_matches_oracle(shape, mode, force):
     f0 = near_eq(nx, ny, nx * 10 + ny + mode + 3 * force)
     Fv = (2e-4, -3e-4) if force else (0.0, 0.0)
     rng = np.random.default_rng(nx + ny)
-    om = rng.uniform(0.3, 1.9, 9)
+    om = rng.uniform(0.6, 1.6, 9)  # moderate rates: the rough random state stays stable for 48 steps
+    om[5] = om[4]  # isotropic shear viscosity
     with F.Lattice2D(nx, ny, "fp64") as lat:
         lat.set_params(1.0, 0.0, 0.0, mode)
         lat.set_rates(om)

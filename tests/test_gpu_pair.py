@@ -63,3 +63,4 @@ def test_pair_equals_single_variant(monkeypatch, prec, shape):
     d = np.abs(a - b)
     assert np.max(d) <= 40 * 1e-7 + 8 * ulp
     assert np.mean(d) <= 40 * 1e-8 + 0.25 * ulp
+

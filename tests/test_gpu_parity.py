@@ -296,6 +296,19 @@ def test_full_size_tgv_256_fp32_sampled():
         _check_sampled(lat, (n, n, n), 0, (0, 0, 0), O.rates(tau), 0.0, seed=1)
 
 
+@pytest.mark.parametrize("prec,unit", [("fp32", 0.0), ("fp16", 2.0 ** -11)])
+def test_full_size_tgv_512_sampled(prec, unit):
+    """Config: TGV Re = 1600 at 512^3 (14.5 GB FP32, 7.2 GB FP16 on the device), sampled cells after
+    one even and one odd step, in the launch configuration the autotuner picks for that size."""
+    n, u0 = 512, 0.05
+    tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
+    rho, ux, uy, uz = W.tgv(n, u0)
+    with make(n, n, n, prec, tau=tau) as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        del rho, ux, uy, uz
+        _check_sampled(lat, (n, n, n), 0, (0, 0, 0), O.rates(tau), unit, seed=3)
+
+
 def test_full_size_channel_bf16_sampled():
     """Config: channel 384 x 192 x 192, walls in y, body force, BF16 storage; sampled cells."""
     nx, ny, nz = 384, 192, 192

@@ -173,3 +173,14 @@ def ensemble_fields(sides, seed: int = 2410):
         moved = [np.roll(np.transpose(comps[perm[i]], perm), shift, axis=(0, 1, 2)) for i in range(3)]
         out.append((np.ones((s, s, s)), moved[2], moved[1], moved[0]))
     return out
+
+
+def shear_layers(L: int, U: float, w: float = 0.05, delta: float = 0.05):
+    """Doubly periodic shear layers on an L x L grid (coordinates scaled by L, cell centres):
+    u_x = U tanh(4 (y - 1/4) / w) for y <= 1/2, U tanh(4 (3/4 - y) / w) above, and
+    u_y = U delta sin(2 pi (x + 1/4)).  Returns (rho, ux, uy) shaped [y, x] with rho = 1."""
+    c = (np.arange(L) + 0.5) / L
+    x, y = np.meshgrid(c, c)
+    ux = np.where(y <= 0.5, U * np.tanh(4 * (y - 0.25) / w), U * np.tanh(4 * (0.75 - y) / w))
+    uy = U * delta * np.sin(2 * np.pi * (x + 0.25))
+    return np.ones((L, L)), ux, uy
