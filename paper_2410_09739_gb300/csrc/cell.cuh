@@ -167,4 +167,39 @@ __device__ __forceinline__ void update_cell(S* __restrict__ buf, const CellGeom&
     for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, cell), g[s]);
 }
 
+// Two cells per thread (see pair.cuh): cells c1 and c2 (c2 only when two) are
+// loaded into the lanes of f2 values, collided with packed fp32 arithmetic and
+// stored back, each cell at its own AA addresses.  Resting walls only.
+template <typename S, bool ODD, int BC, bool FORCE, int MODE>
+__device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom& G, unsigned c1, unsigned c2,
+                                            bool two, const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5,
+                                            f2 om6, f2 om8, f2 om9, int* flag)
+{
+    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_HALF_CHANNEL, "resting walls only");
+    const unsigned stride = G.stride;
+    if (!two) c2 = c1;
+    f2 g[27];
+    {
+        Nbr n;
+        if (ODD) n = make_nbr<BC>(G, c1);
+#pragma unroll
+        for (int s = 0; s < 27; ++s) g[s].v.x = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, c1));
+        if (ODD) n = make_nbr<BC>(G, c2);
+#pragma unroll
+        for (int s = 0; s < 27; ++s) g[s].v.y = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, c2));
+    }
+    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
+    if (!ok) atomicOr(flag, 1);
+    asm volatile("" : "+r"(c1));  // rebuild the store addresses (see update_cell)
+    Nbr n;
+    if (ODD) n = make_nbr<BC>(G, c1);
+#pragma unroll
+    for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c1), g[s].v.x);
+    if (two) {
+        if (ODD) n = make_nbr<BC>(G, c2);
+#pragma unroll
+        for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c2), g[s].v.y);
+    }
+}
+
 }  // namespace fpc

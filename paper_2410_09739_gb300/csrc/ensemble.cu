@@ -46,21 +46,62 @@ __global__ void __launch_bounds__(256, MINB) k_ens_step(const EnsArgs a)
     }
 }
 
-template <bool ODD, bool FORCE, int MODE>
-static cudaError_t go(const EnsArgs& a, int block, int minb, int grid, cudaStream_t st)
+// Paired variant: a tile's cells t and t + tile/2 share a thread (pair.cuh).
+template <bool ODD, bool FORCE, int MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_ens_pair(const EnsArgs a)
 {
-    if (minb == 3)
+    float* __restrict__ base = static_cast<float*>(a.buf);
+    const unsigned half = a.tile_cells / 2;
+    for (unsigned t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const unsigned b = __ldg(a.tile_box + t);
+        const EnsBox& B = a.boxes[b];
+        const unsigned first = (t - __ldg(&B.tile0)) * a.tile_cells;
+        const unsigned ncells = __ldg(&B.ncells);
+        CellGeom G;
+        G.stride = __ldg(&B.stride);
+        G.nx = __ldg(&B.nx);
+        G.ny = __ldg(&B.ny);
+        G.nz = __ldg(&B.nz);
+        G.div_nx.d = __ldg(&B.div_nx.d);
+        G.div_nx.m = __ldg(&B.div_nx.m);
+        G.div_nx.s = __ldg(&B.div_nx.s);
+        G.div_nxny.d = __ldg(&B.div_nxny.d);
+        G.div_nxny.m = __ldg(&B.div_nxny.m);
+        G.div_nxny.s = __ldg(&B.div_nxny.s);
+        const float om = __ldg(&B.om_shear);
+        const f2 om2(om, om);
+        float* buf = base + __ldg(&B.off);
+        for (unsigned c = threadIdx.x; c < half; c += blockDim.x) {
+            const unsigned c1 = first + c, c2 = c1 + half;
+            if (c1 >= ncells) break;
+            update_pair<float, ODD, BC_PERIODIC, FORCE, MODE>(buf, G, c1, c2, c2 < ncells, a.rates2, a.Fx2, a.Fy2,
+                                                              a.Fz2, om2, om2, om2, om2, om2, a.flag);
+        }
+    }
+}
+
+template <bool ODD, bool FORCE, int MODE>
+static cudaError_t go(const EnsArgs& a, int block, int minb, int grid, int variant, cudaStream_t st)
+{
+    if (variant == 2) {
+        if (block != 128 || a.tile_cells % (2 * block) != 0) return cudaErrorInvalidValue;
+        if (minb == 3)
+            k_ens_pair<ODD, FORCE, MODE, 3><<<grid, block, 0, st>>>(a);
+        else
+            k_ens_pair<ODD, FORCE, MODE, 4><<<grid, block, 0, st>>>(a);
+    } else if (minb == 3) {
         k_ens_step<ODD, FORCE, MODE, 3><<<grid, block, 0, st>>>(a);
-    else
+    } else {
         k_ens_step<ODD, FORCE, MODE, 2><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_ens_step(int odd, int force, int mode, const EnsArgs& a, int block, int minb, int grid,
-                            cudaStream_t st)
+                            int variant, cudaStream_t st)
 {
     if (grid <= 0 || block <= 0 || block > 256 || a.tile_cells % block != 0) return cudaErrorInvalidValue;
-#define FPC_ENS(O, Fo, M) return go<O, Fo, M>(a, block, minb, grid, st)
+#define FPC_ENS(O, Fo, M) return go<O, Fo, M>(a, block, minb, grid, variant, st)
     if (mode == MODE_FP) {
         if (odd) { if (force) FPC_ENS(true, true, MODE_FP); FPC_ENS(true, false, MODE_FP); }
         if (force) FPC_ENS(false, true, MODE_FP);
@@ -75,11 +116,17 @@ cudaError_t launch_ens_step(int odd, int force, int mode, const EnsArgs& a, int 
     return cudaErrorInvalidValue;
 }
 
-int ens_max_blocks_per_sm(int block, int minb, int mode)
+int ens_max_blocks_per_sm(int block, int minb, int mode, int variant)
 {
     int n = 0;
     cudaError_t e;
-    if (mode == MODE_EQ)
+    if (variant == 2 && minb == 3)
+        e = mode == MODE_EQ ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_EQ, 3>, block, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_FP, 3>, block, 0);
+    else if (variant == 2)
+        e = mode == MODE_EQ ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_EQ, 4>, block, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_FP, 4>, block, 0);
+    else if (mode == MODE_EQ)
         e = minb == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_EQ, 3>, block, 0)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_EQ, 2>, block, 0);
     else
@@ -207,7 +254,7 @@ extern "C" int fpclbm_create_ensemble(fpclbm_t* out, int n_boxes, const int* dim
     }
     h->block = tile;
     h->minb = 2;
-    h->grid = h->sm_count * ens_max_blocks_per_sm(tile, 2, MODE_FP);
+    h->grid = h->sm_count * ens_max_blocks_per_sm(tile, 2, MODE_FP, 0);
     *out = h;
     return FPCLBM_OK;
 }

@@ -166,6 +166,14 @@ EnsArgs make_ens_args(const fpclbm* h)
     a.Fx = (float)h->F[0];
     a.Fy = (float)h->F[1];
     a.Fz = (float)h->F[2];
+    for (int j = 0; j < 27; ++j) {
+        a.rates2.om[j] = f2(a.rates.om[j], a.rates.om[j]);
+        a.rates2.keep[j] = f2(a.rates.keep[j], a.rates.keep[j]);
+        a.rates2.src[j] = f2(a.rates.src[j], a.rates.src[j]);
+    }
+    a.Fx2 = f2(a.Fx, a.Fx);
+    a.Fy2 = f2(a.Fy, a.Fy);
+    a.Fz2 = f2(a.Fz, a.Fz);
     a.flag = h->d_flag;
     return a;
 }
@@ -240,7 +248,7 @@ int upload_smag(fpclbm* h)
 cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st, int block, int minb, int grid, int pipe)
 {
     if (h->ensemble)
-        return launch_ens_step((int)(t & 1), has_force(h), mode_of(h), make_ens_args(h), block, minb, grid, st);
+        return launch_ens_step((int)(t & 1), has_force(h), mode_of(h), make_ens_args(h), block, minb, grid, pipe, st);
     const StepArgs<double> a64 = make_args<double>(h);
     const StepArgs<float> a32 = make_args<float>(h);
     StepLaunch cfg{block, minb, pipe};
@@ -366,11 +374,11 @@ int autotune(fpclbm* h)
 {
     h->tuned = true;
     std::vector<TuneChoice> cands;
-    // register-cap variants: fp32 arithmetic, FP/EQ modes, resting walls; pipelined variant: the
+    // register-cap variants: fp32 arithmetic, FP/EQ modes, any boundary; pipelined variant: the
     // same on periodic and channel boxes with 4- or 8-byte storage (cp.async moves >= 4 bytes)
     const int kb = kernel_bc(h), md = mode_of(h);
     const bool fixed_walls = bc_fixed(kb);
-    const bool fp32_math = h->precision != FPCLBM_FP64 && (md == MODE_FP || md == MODE_EQ) && fixed_walls;
+    const bool fp32_math = h->precision != FPCLBM_FP64 && (md == MODE_FP || md == MODE_EQ);
     const bool pipe_ok = elem_size(h->precision) >= 4 && (md == MODE_FP || md == MODE_EQ) &&
                          (kb == BC_PERIODIC || kb == BC_WALLS_Y);
     // paired variant (two cells per thread, packed fp32): fp32 arithmetic, periodic and channel
@@ -378,9 +386,13 @@ int autotune(fpclbm* h)
     if (h->ensemble) {
         for (int minb : {2, 3})
             for (int block : {128, 256}) {
-                const int per_sm = ens_max_blocks_per_sm(block, minb, mode_of(h));
+                const int per_sm = ens_max_blocks_per_sm(block, minb, mode_of(h), 0);
                 for (int mult : {1, 2}) cands.push_back({block, minb, h->sm_count * per_sm * mult, 0});
             }
+        for (int minb : {3, 4}) {  // paired variant: 3 or 4 blocks of 128 threads per SM
+            const int per_sm = ens_max_blocks_per_sm(128, minb, mode_of(h), 2);
+            for (int mult : {1, 2}) cands.push_back({128, minb, h->sm_count * per_sm * mult, 2});
+        }
     } else if (fp32_math) {
         for (int minb : {2, 3, 4})
             for (int block : {128, 256}) cands.push_back({block, minb, 0, 0});
@@ -396,6 +408,23 @@ int autotune(fpclbm* h)
         if (pipe_ok) cands.push_back({128, 1, 0, 1});
     }
     TuneChoice forced;
+    if (h->ensemble && forced_launch(forced)) {
+        // ensembles: variant 0 (one cell per thread, minb 2 or 3) or 2 (paired, blocks of 128,
+        // minb 3 or 4); persistent grid from the occupancy of the chosen kernel
+        if (forced.pipe == 2) {
+            forced.block = 128;
+            if (forced.minb != 3) forced.minb = 4;
+        } else {
+            forced.pipe = 0;
+            if (forced.minb != 3) forced.minb = 2;
+            if (h->tile_cells % forced.block) forced.block = h->tile_cells;
+        }
+        h->block = forced.block;
+        h->minb = forced.minb;
+        h->pipe = forced.pipe;
+        h->grid = h->sm_count * ens_max_blocks_per_sm(forced.block, forced.minb, mode_of(h), forced.pipe);
+        return FPCLBM_OK;
+    }
     if (!h->ensemble && forced_launch(forced)) {
         if ((forced.pipe == 1 && !pipe_ok) || (forced.pipe == 2 && !pair_ok)) forced.pipe = 0;
         if (forced.pipe == 2) forced.minb = 2;

@@ -11,6 +11,7 @@
 
 #include "fpclbm.h"  // include/ is on the include path
 #include "internal.h"
+#include "pair.cuh"
 
 namespace fpc {
 
@@ -39,16 +40,19 @@ struct EnsArgs {
     const EnsBox* boxes;
     const unsigned* tile_box;
     unsigned ntiles;
-    unsigned tile_cells;  // cells per tile (a multiple of the block size)
+    unsigned tile_cells;  // cells per tile (a multiple of the block size; of twice it when paired)
     Rates<float> rates;
     float Fx, Fy, Fz;
+    Rates<f2> rates2;     // the same, duplicated into both lanes (paired variant)
+    f2 Fx2, Fy2, Fz2;
     int* flag;
 };
 
-// Ensemble step launch (ensemble.cu).  grid = persistent blocks.
+// Ensemble step launch (ensemble.cu).  grid = persistent blocks; variant 2 =
+// two cells per thread (blocks of 128 threads, tiles of 256 cells).
 cudaError_t launch_ens_step(int odd, int force, int mode, const EnsArgs& a, int block, int minb, int grid,
-                            cudaStream_t st);
-int ens_max_blocks_per_sm(int block, int minb, int mode);
+                            int variant, cudaStream_t st);
+int ens_max_blocks_per_sm(int block, int minb, int mode, int variant);
 
 }  // namespace fpc
 

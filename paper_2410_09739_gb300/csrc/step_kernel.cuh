@@ -147,9 +147,8 @@ cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
 template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, unsigned half)
 {
-    unsigned c1 = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned c1 = blockIdx.x * blockDim.x + threadIdx.x;
     if (c1 >= half) return;
-    const bool two = c1 + half < a.ncells;
     CellGeom G;
     G.stride = a.stride;
     G.nx = a.nx;
@@ -157,34 +156,9 @@ __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, u
     G.nz = a.nz;
     G.div_nx = a.div_nx;
     G.div_nxny = a.div_nxny;
-    S* __restrict__ buf = static_cast<S*>(a.buf);
-    const unsigned stride = a.stride;
-    f2 g[27];
-    {
-        Nbr n;
-        if (ODD) n = make_nbr<BC>(G, c1);
-#pragma unroll
-        for (int s = 0; s < 27; ++s) g[s].v.x = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, c1));
-        const unsigned c2 = two ? c1 + half : c1;
-        if (ODD) n = make_nbr<BC>(G, c2);
-#pragma unroll
-        for (int s = 0; s < 27; ++s) g[s].v.y = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, c2));
-    }
     const Rates<f2>& rt = a.rates;
-    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, a.Fx, a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6], rt.om[8],
-                                                  rt.om[9], nullptr);
-    if (!ok) atomicOr(a.flag, 1);
-    asm volatile("" : "+r"(c1));  // rebuild the store addresses (see update_cell)
-    Nbr n;
-    if (ODD) n = make_nbr<BC>(G, c1);
-#pragma unroll
-    for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c1), g[s].v.x);
-    if (two) {
-        const unsigned c2 = c1 + half;
-        if (ODD) n = make_nbr<BC>(G, c2);
-#pragma unroll
-        for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c2), g[s].v.y);
-    }
+    update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, c1 + half, c1 + half < a.ncells, rt, a.Fx,
+                                         a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
 }
 
 // The launch arguments with every scalar duplicated into both lanes.
@@ -242,19 +216,20 @@ cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st
     return cudaGetLastError();
 }
 
-// Register-cap variants exist for the fp32-arithmetic modes on boxes with
-// resting walls: 2, 3, 4 for FP and EQ; 1 (no cap) and 2 (128 registers) for
-// the learned mode, whose tensor-core MLP keeps the cell's state live.  fp64,
-// the Smagorinsky mode and moving walls have one variant each.
+// Register-cap variants exist for fp32 arithmetic: 2, 3, 4 for the FP and EQ
+// modes (every boundary kind); 1 (no cap) and 2 (128 registers) for the
+// learned mode on boxes with resting walls, whose tensor-core MLP keeps the
+// cell's state live.  fp64 and the Smagorinsky mode have one variant each.
 template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE>
 cudaError_t step_by_minb(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
-    constexpr bool fp32_fixed = sizeof(R) == 4 && bc_fixed(BC) && MODE != MODE_SMAG;
-    if constexpr (fp32_fixed && MODE != MODE_LEARNED) {
+    constexpr bool fp32_capped = sizeof(R) == 4 && (MODE == MODE_FP || MODE == MODE_EQ);
+    constexpr bool fp32_learned = sizeof(R) == 4 && MODE == MODE_LEARNED && bc_fixed(BC);
+    if constexpr (fp32_capped) {
         if (cfg.minb == 3) return step_go<S, R, ODD, BC, FORCE, MODE, 3>(a, cfg, st);
         if (cfg.minb == 4) return step_go<S, R, ODD, BC, FORCE, MODE, 4>(a, cfg, st);
         return step_go<S, R, ODD, BC, FORCE, MODE, 2>(a, cfg, st);
-    } else if constexpr (fp32_fixed) {
+    } else if constexpr (fp32_learned) {
         if (cfg.minb == 2) return step_go<S, R, ODD, BC, FORCE, MODE, 2>(a, cfg, st);
         return step_go<S, R, ODD, BC, FORCE, MODE, 1>(a, cfg, st);
     } else {

@@ -23,8 +23,13 @@ def concat(fs):
     return [np.concatenate([f[q].reshape(-1) for f in fs]) for q in range(4)]
 
 
+@pytest.mark.parametrize("launch", ["", "128:4:2", "128:3:2"])
 @pytest.mark.parametrize("nsteps", [1, 2, 7, 40])
-def test_each_box_matches_oracle_and_single_box(nsteps):
+def test_each_box_matches_oracle_and_single_box(monkeypatch, nsteps, launch):
+    """launch: the default configuration, or the paired kernel (two cells of a tile per thread) with
+    either register cap, forced through FPCLBM_LAUNCH.  The boxes' last tiles are ragged, so some
+    threads hold one cell."""
+    monkeypatch.setenv("FPCLBM_LAUNCH", launch)
     fs = fields(10 * nsteps)
     with F.Lattice.ensemble(DIMS, TAUS, "fp32") as ens:
         ens.set_params(1.0)
