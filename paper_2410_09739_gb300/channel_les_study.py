@@ -16,7 +16,13 @@ u+ = ln(y+) / 0.41 + 5.2 in the log layer (30 < y+ < 0.3 Re*), and the total she
 checked against its exact linear profile u*^2 (1 - y/H) (momentum balance of the statistically
 steady channel: viscous + resolved Reynolds + subgrid stress).
 
-Usage: python -m paper_2410_09739_gb300.channel_les_study [--H 64] [--re-tau 180] ...
+--full runs the full channel of the channel configuration instead: walls at y = -1/2 and
+2H - 1/2, domain --domain nx ny nz (default 4H x 2H x 2H, i.e. 384 x 192 x 192 at H = 96), the
+same initial state mirrored into the upper half, BF16 storage by default; statistics fold the two
+halves (u, w even and v odd about the centre plane) and the momentum-balance residual
+max |nu dU/dy - <u'v'> - u*^2 (1 - y/H)| / u*^2 over the half height is reported.
+
+Usage: python -m paper_2410_09739_gb300.channel_les_study [--H 64] [--re-tau 180] [--full] ...
 Prints one JSON object.
 """
 from __future__ import annotations
@@ -50,6 +56,8 @@ def parse(argv=None):
     p.add_argument("--precision", default="fp32")
     p.add_argument("--model", default="smagorinsky", choices=["smagorinsky", "none"])
     p.add_argument("--vortices", type=float, default=4.0, help="streak/vortex amplitude in units of u*")
+    p.add_argument("--full", action="store_true", help="full channel with two walls (channel configuration)")
+    p.add_argument("--domain", type=int, nargs=3, default=None, help="nx ny nz (full channel)")
     p.add_argument("--seed", type=int, default=7)
     return p.parse_args(argv)
 
@@ -73,25 +81,33 @@ def run(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream().cuda_stream
     H = args.H
-    nx, ny, nz = int(round(2 * math.pi * H)), H, int(round(math.pi * H))
+    if args.full:
+        nx, ny, nz = args.domain if args.domain else (4 * H, 2 * H, 2 * H)
+        assert ny == 2 * H, "full channel: ny = 2H"
+    else:
+        nx, ny, nz = int(round(2 * math.pi * H)), H, int(round(math.pi * H))
     us = args.u_star
     nu = us * H / args.re_tau
     tau = 3.0 * nu + 0.5
     Fx = us * us / H
     Tstar = H / us
-    lat = F.Lattice(nx, ny, nz, args.precision, F.FPCLBM_BC_HALF_CHANNEL, stream=stream)
+    lat = F.Lattice(nx, ny, nz, args.precision, F.FPCLBM_BC_WALLS_Y if args.full else F.FPCLBM_BC_HALF_CHANNEL,
+                    stream=stream)
     if args.model == "smagorinsky":
         lat.set_params(tau, 0.0, F.FPCLBM_DIFF_FP_SMAGORINSKY)
         lat.set_smagorinsky(args.cs, us, args.a_plus)
     else:
         lat.set_params(tau)
     lat.set_force(Fx, 0.0, 0.0)
-    rho, ux, uy, uz = (np.ascontiguousarray(a[:, :ny, :]) for a in W.channel_fields(nx, 2 * ny, nz, us,
-                                                                                       seed=args.seed))
+    rho, ux, uy, uz = (np.ascontiguousarray(a[:, :H, :]) for a in W.channel_fields(nx, 2 * H, nz, us,
+                                                                                      seed=args.seed))
     if args.vortices > 0:
-        du, dv, dw = perturbation(nx, ny, nz, H, args.vortices * us)
+        du, dv, dw = perturbation(nx, H, nz, H, args.vortices * us)
         ux, uy, uz = ux + du, uy + dv, uz + dw
-    lat.init_fields(rho, ux, uy, uz)
+    if args.full:  # mirror image in the upper half: u, w even, v odd about the centre plane
+        rho, ux, uz = (np.concatenate([a, a[:, ::-1, :]], axis=1) for a in (rho, ux, uz))
+        uy = np.concatenate([uy, -uy[:, ::-1, :]], axis=1)
+    lat.init_fields(*(np.ascontiguousarray(a) for a in (rho, ux, uy, uz)))
 
     t0 = time.perf_counter()
     n_spin = int(round(args.spinup * Tstar))
@@ -126,13 +142,17 @@ def run(args):
     coll_s = time.perf_counter() - t0
     m = {k: (a / samples).cpu().numpy() for k, a in acc.items()}
     lat.close()
+    if args.full:  # fold the upper half onto the lower one
+        for k in m:
+            sgn = -1.0 if k in ("v", "uv") else 1.0
+            m[k] = 0.5 * (m[k][:H] + sgn * m[k][::-1][:H])
 
     U, V, Wm = m["u"], m["v"], m["w"]
     urms = np.sqrt(np.maximum(m["uu"] - U * U, 0))
     vrms = np.sqrt(np.maximum(m["vv"] - V * V, 0))
     wrms = np.sqrt(np.maximum(m["ww"] - Wm * Wm, 0))
     uv = m["uv"] - U * V
-    y = np.arange(ny) + 0.5  # distance of the row centre from the wall
+    y = np.arange(H) + 0.5  # distance of the row centre from the wall
     yplus = y * us / nu
     uplus = U / us
     law = np.where(yplus < 5, yplus, np.where(yplus > 30, np.log(np.maximum(yplus, 1e-30)) / 0.41 + 5.2, np.nan))
@@ -144,7 +164,8 @@ def run(args):
     exact = us * us * (1 - y / H)
     steps = n_spin + n_coll
     return {
-        "study": "half-channel LES, FPC-LBM + Smagorinsky/van Driest",
+        "study": ("full channel, FPC-LBM" if args.full else "half channel, FPC-LBM") +
+                 (" + Smagorinsky/van Driest LES" if args.model == "smagorinsky" else ""),
         "config": {"domain": [nx, ny, nz], "H": H, "re_tau": args.re_tau, "u_star": us, "nu": nu, "tau": tau,
                    "Fx": Fx, "Cs": args.cs if args.model == "smagorinsky" else 0.0, "A_plus": args.a_plus,
                    "friction_time_steps": Tstar, "spinup_T": args.spinup, "collect_T": args.collect,
@@ -156,6 +177,7 @@ def run(args):
         "log_layer_max_abs_dev_u_plus": float(np.nanmax(np.abs(uplus[logr] - law[logr]))) if logr.any() else None,
         "log_layer_rows": int(logr.sum()),
         "resolved_stress_over_total_at_y_H_0p5": float(np.interp(0.5 * H, y, resolved / np.maximum(exact, 1e-30))),
+        "momentum_balance_max_residual_over_u_star2": float(np.max(np.abs(resolved - exact)) / us**2),
         "y_plus": [round(float(v), 3) for v in yplus],
         "u_plus": [round(float(v), 4) for v in uplus],
         "urms_plus": [round(float(v), 4) for v in urms / us],
