@@ -9,7 +9,9 @@ Steps (all simulation, filtering and training on the GPU through the C ABI):
   3. train the closure network on the collected samples (fpclbm_closure_train);
   4. coarse runs (acoustic scaling: dx, dt x r, nu / r, F x r), started from the
      filtered fine velocity at the start of the window, over the same physical
-     time, plain FPC-LBM and FPC-LBM + closure, accumulating U(y);
+     time: plain FPC-LBM, FPC-LBM + learned closure, and FPC-LBM + the paper's
+     Smagorinsky/van Driest subgrid model (Sec. 4) as the non-learned baseline,
+     accumulating U(y);
   5. L2-relative profile error of each coarse run against the filtered fine
      profile, and the wall-clock speed-up of the coarse run over the fine run
      for equal physical time on the same GPU.
@@ -49,6 +51,7 @@ def parse(argv=None):
     p.add_argument("--lr", type=float, default=2e-3)
     p.add_argument("--precision", default="bf16")
     p.add_argument("--seed", type=int, default=7)
+    p.add_argument("--cs", type=float, default=0.1, help="Smagorinsky constant of the non-learned baseline")
     return p.parse_args(argv)
 
 
@@ -150,11 +153,14 @@ def run(args):
               np.ascontiguousarray(u0[:, 2]))
     n_coarse = int(round(n_snap * args.snap * Tc))
     coarse_res = {}
-    for name in ("plain", "learned"):
+    for name in ("plain", "learned", "smagorinsky"):
         lat = F.Lattice(nxc, nyc, nzc, args.precision, F.FPCLBM_BC_WALLS_Y, stream=stream)
         if name == "learned":
             lat.set_closure(w)
             lat.set_params(tau_c, 0.0, F.FPCLBM_DIFF_FP_LEARNED)
+        elif name == "smagorinsky":  # the paper's own subgrid model (Sec. 4) as the non-learned baseline
+            lat.set_params(tau_c, 0.0, F.FPCLBM_DIFF_FP_SMAGORINSKY)
+            lat.set_smagorinsky(args.cs, us, 26.0)  # acoustic scaling: u* is the same in coarse lattice units
         else:
             lat.set_params(tau_c)
         lat.set_force(Fc, 0.0, 0.0)
