@@ -18,7 +18,7 @@ steady channel: viscous + resolved Reynolds + subgrid stress).
 
 --full runs the full channel of the channel configuration instead: walls at y = -1/2 and
 2H - 1/2, domain --domain nx ny nz (default 4H x 2H x 2H, i.e. 384 x 192 x 192 at H = 96), the
-same initial state mirrored into the upper half, BF16 storage by default; statistics fold the two
+laminar profile with noise and streaks/vortices spanning the whole height; statistics fold the two
 halves (u, w even and v odd about the centre plane) and the momentum-balance residual
 max |nu dU/dy - <u'v'> - u*^2 (1 - y/H)| / u*^2 over the half height is reported.
 
@@ -62,14 +62,21 @@ def parse(argv=None):
     return p.parse_args(argv)
 
 
-def perturbation(nx, ny, nz, H, amp):
-    """Streaks u' ~ sin(pi y / 2H) cos(k_z z) and vortices v' ~ sin(pi y / H) sin(k_z z) cos(k_x x),
-    w' ~ cos(pi y / H) cos(k_z z) sin(k_x x): zero u', v' at the wall, zero v' and du'/dy at the
-    symmetry plane."""
+def perturbation(nx, ny, nz, H, amp, full=False):
+    """Large-scale streaks and streamwise vortices (spanwise wavenumber 4, streamwise 2).
+    Half channel (wall at y = 0, symmetry plane at y = H): u' ~ sin(pi y / 2H) cos(k_z z),
+    v' ~ sin(pi y / H) sin(k_z z) cos(k_x x), w' ~ cos(pi y / H) cos(k_z z) sin(k_x x) -- zero u',
+    v' at the wall, zero v' and du'/dy at the symmetry plane.  full (walls at y = 0 and y = H):
+    every component ~ sin(pi y / H), so v' crosses the centre plane and breaks the mirror symmetry
+    of the laminar state."""
     x = 2 * math.pi * np.arange(nx) / nx
     z = 2 * math.pi * np.arange(nz) / nz
     y = (np.arange(ny) + 0.5) / H
     Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    if full:
+        shape = np.sin(math.pi * Y)
+        return (amp * shape * np.cos(4 * Z), 0.5 * amp * shape * np.sin(4 * Z) * np.cos(2 * X),
+                0.5 * amp * shape * np.cos(4 * Z) * np.sin(2 * X))
     du = amp * np.sin(0.5 * math.pi * Y) * np.cos(4 * Z)
     dv = 0.5 * amp * np.sin(math.pi * Y) * np.sin(4 * Z) * np.cos(2 * X)
     dw = 0.5 * amp * np.cos(math.pi * Y) * (1 - np.exp(-8 * Y)) * np.cos(4 * Z) * np.sin(2 * X)
@@ -101,12 +108,14 @@ def run(args):
     lat.set_force(Fx, 0.0, 0.0)
     rho, ux, uy, uz = (np.ascontiguousarray(a[:, :H, :]) for a in W.channel_fields(nx, 2 * H, nz, us,
                                                                                       seed=args.seed))
-    if args.vortices > 0:
+    if args.full:  # the whole laminar channel, then perturbations spanning both halves
+        rho, ux, uy, uz = W.channel_fields(nx, 2 * H, nz, us, seed=args.seed)
+        if args.vortices > 0:
+            du, dv, dw = perturbation(nx, 2 * H, nz, 2 * H, args.vortices * us, full=True)
+            ux, uy, uz = ux + du, uy + dv, uz + dw
+    elif args.vortices > 0:
         du, dv, dw = perturbation(nx, H, nz, H, args.vortices * us)
         ux, uy, uz = ux + du, uy + dv, uz + dw
-    if args.full:  # mirror image in the upper half: u, w even, v odd about the centre plane
-        rho, ux, uz = (np.concatenate([a, a[:, ::-1, :]], axis=1) for a in (rho, ux, uz))
-        uy = np.concatenate([uy, -uy[:, ::-1, :]], axis=1)
     lat.init_fields(*(np.ascontiguousarray(a) for a in (rho, ux, uy, uz)))
 
     t0 = time.perf_counter()
