@@ -167,19 +167,21 @@ __device__ __forceinline__ void update_cell(S* __restrict__ buf, const CellGeom&
     for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, cell), g[s]);
 }
 
-// Two cells per thread (see pair.cuh): cells c1 and c2 (c2 only when two) are
-// loaded into the lanes of f2 values, collided with packed fp32 arithmetic and
-// stored back, each cell at its own AA addresses.  Resting walls only.
+// Two cells per thread (see pair.cuh): cells c1 and c2 = c1 + half (c2 only
+// when it is below ncells) are loaded into the lanes of f2 values, collided
+// with packed fp32 arithmetic and stored back, each cell at its own AA
+// addresses.  c2 is recomputed after the collision (from the uniform half)
+// rather than kept live through it.  Resting walls only.
 template <typename S, bool ODD, int BC, bool FORCE, int MODE>
-__device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom& G, unsigned c1, unsigned c2,
-                                            bool two, const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5,
-                                            f2 om6, f2 om8, f2 om9, int* flag)
+__device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom& G, unsigned c1, unsigned half,
+                                            unsigned ncells, const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4,
+                                            f2 om5, f2 om6, f2 om8, f2 om9, int* flag)
 {
     static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_HALF_CHANNEL, "resting walls only");
     const unsigned stride = G.stride;
-    if (!two) c2 = c1;
     f2 g[27];
     {
+        const unsigned c2 = c1 + half < ncells ? c1 + half : c1;
         Nbr n;
         if (ODD) n = make_nbr<BC>(G, c1);
 #pragma unroll
@@ -195,7 +197,8 @@ __device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom&
     if (ODD) n = make_nbr<BC>(G, c1);
 #pragma unroll
     for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c1), g[s].v.x);
-    if (two) {
+    const unsigned c2 = c1 + half;
+    if (c2 < ncells) {
         if (ODD) n = make_nbr<BC>(G, c2);
 #pragma unroll
         for (int s = 0; s < 27; ++s) Store<S>::st(store_ptr<S, ODD, BC>(buf, s, n, stride, c2), g[s].v.y);

@@ -72,10 +72,10 @@ __global__ void __launch_bounds__(128, MINB) k_ens_pair(const EnsArgs a)
         const f2 om2(om, om);
         float* buf = base + __ldg(&B.off);
         for (unsigned c = threadIdx.x; c < half; c += blockDim.x) {
-            const unsigned c1 = first + c, c2 = c1 + half;
+            const unsigned c1 = first + c;
             if (c1 >= ncells) break;
-            update_pair<float, ODD, BC_PERIODIC, FORCE, MODE>(buf, G, c1, c2, c2 < ncells, a.rates2, a.Fx2, a.Fy2,
-                                                              a.Fz2, om2, om2, om2, om2, om2, a.flag);
+            update_pair<float, ODD, BC_PERIODIC, FORCE, MODE>(buf, G, c1, half, ncells, a.rates2, a.Fx2, a.Fy2, a.Fz2,
+                                                              om2, om2, om2, om2, om2, a.flag);
         }
     }
 }

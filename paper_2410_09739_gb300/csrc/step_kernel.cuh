@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, u
     G.div_nx = a.div_nx;
     G.div_nxny = a.div_nxny;
     const Rates<f2>& rt = a.rates;
-    update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, c1 + half, c1 + half < a.ncells, rt, a.Fx,
-                                         a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
+    update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, half, a.ncells, rt, a.Fx, a.Fy, a.Fz,
+                                         rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
 }
 
 // The launch arguments with every scalar duplicated into both lanes.
