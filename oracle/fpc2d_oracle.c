@@ -20,7 +20,9 @@
  *     (3: 2s bulk, 4: 2d and 5: 11 shear, 6: 21, 7: 12, 8: 22);
  *   - chain order: orders <= 2, then 3, then 4 (the fourth-order attractor
  *     uses post-collision second moments, reading R2);
- *   - half-force velocity of Step 7, periodic push streaming of Step 6.
+ *   - half-force velocity of Step 7, push streaming of Step 6, periodic or in
+ *     a closed square box with half-way bounce-back and a moving lid (the 2D
+ *     lid-driven cavity of Sec. 4).
  * mode 1 (MCM): Maxwellian central moments at every order (reading R3).
  *
  * Arrays: f[a][y][x], a = 0..8 (alpha-major), full populations, fp64.
@@ -230,35 +232,72 @@ int orc2_init_equilibrium(int nx, int ny, const double* rho, const double* ux, c
 
 static long wrap2(long i, long n) { return ((i % n) + n) % n; }
 
-/* One step: collide, then periodic push streaming f_a(x + e_a) = f~_a(x). */
-int orc2_step(int nx, int ny, const double* fin, double* fout, const double F[2], const double omega[Q2], int mode)
+/* One step: collide, then push streaming f_a(x + e_a) = f~_a(x).
+ * bc = 0: periodic; bc = 2: closed square box, half-way bounce-back at -1/2
+ * and n - 1/2 on both axes, the wall y = ny - 1/2 moving along x at uw (the
+ * 2D lid-driven cavity of Sec. 4): a population leaving cell x towards a
+ * solid point is reflected into the opposite direction at x, and through the
+ * moving wall (destination row y = ny, corners included) it carries the
+ * momentum correction -2 w_a rho(x) e_ax uw / cs^2 (as in 3D, reading R6). */
+int orc2_step_bc(int nx, int ny, int bc, const double* fin, double* fout, const double F[2], const double omega[Q2],
+                 int mode, double uw)
 {
     const long N = (long)nx * ny;
+    if ((bc != 0 && bc != 2) || (bc == 0 && uw != 0)) return -2;
+    int opp[Q2];
+    for (int a = 0; a < Q2; ++a)
+        for (int b = 0; b < Q2; ++b)
+            if (EX2[b] == -EX2[a] && EY2[b] == -EY2[a]) opp[a] = b;
+    double w[Q2];
+    const double zero[2] = {0, 0};
+    if (orc2_equilibrium(1.0, zero, w) != 0) return -1;
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             const long c = x + (long)nx * y;
-            double f[Q2], ft[Q2];
-            for (int a = 0; a < Q2; ++a) f[a] = fin[a * N + c];
+            double f[Q2], ft[Q2], rho = 0;
+            for (int a = 0; a < Q2; ++a) {
+                f[a] = fin[a * N + c];
+                rho += f[a];
+            }
             if (orc2_collide(f, F, omega, mode, ft) != 0) bad |= 1;
-            for (int a = 0; a < Q2; ++a)
-                fout[a * N + wrap2(x + EX2[a], nx) + nx * wrap2(y + EY2[a], ny)] = ft[a];
+            for (int a = 0; a < Q2; ++a) {
+                const long xd = x + EX2[a], yd = y + EY2[a];
+                if (bc == 2 && (xd < 0 || xd >= nx || yd < 0 || yd >= ny)) {
+                    double v = ft[a];
+                    if (yd == ny) v -= 2.0 * w[a] * rho * EX2[a] * uw / CS2_2D;
+                    fout[opp[a] * N + c] = v;
+                    continue;
+                }
+                fout[a * N + wrap2(xd, nx) + nx * wrap2(yd, ny)] = ft[a];
+            }
         }
     return bad ? -1 : 0;
 }
 
-int orc2_run(int nx, int ny, double* f, double* work, const double F[2], const double omega[Q2], int mode, long n)
+int orc2_step(int nx, int ny, const double* fin, double* fout, const double F[2], const double omega[Q2], int mode)
+{
+    return orc2_step_bc(nx, ny, 0, fin, fout, F, omega, mode, 0.0);
+}
+
+int orc2_run_bc(int nx, int ny, int bc, double* f, double* work, const double F[2], const double omega[Q2], int mode,
+                long n, double uw)
 {
     const long N = (long)nx * ny;
     double *a = f, *b = work;
     int rc = 0;
     for (long t = 0; t < n && rc == 0; ++t) {
-        rc = orc2_step(nx, ny, a, b, F, omega, mode);
+        rc = orc2_step_bc(nx, ny, bc, a, b, F, omega, mode, uw);
         double* tmp = a; a = b; b = tmp;
     }
     if (a != f) memcpy(f, a, sizeof(double) * Q2 * N);
     return rc;
+}
+
+int orc2_run(int nx, int ny, double* f, double* work, const double F[2], const double omega[Q2], int mode, long n)
+{
+    return orc2_run_bc(nx, ny, 0, f, work, F, omega, mode, n, 0.0);
 }
 
 void orc2_moments(int nx, int ny, const double* f, const double F[2], double* rho, double* ux, double* uy)

@@ -13,7 +13,7 @@ import numpy as np
 from .oracle import lib as _lib3
 
 __all__ = ["velocity_set", "central_matrix", "grouping_matrix", "attractor_generic", "collide", "equilibrium",
-           "init_equilibrium", "step", "run", "moments", "rates"]
+           "init_equilibrium", "step", "run", "moments", "rates", "BC_PERIODIC", "BC_BOX"]
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
@@ -34,10 +34,12 @@ def lib():
         L.orc2_equilibrium.restype = ctypes.c_int
         L.orc2_init_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
         L.orc2_init_equilibrium.restype = ctypes.c_int
-        L.orc2_step.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_int]
-        L.orc2_step.restype = ctypes.c_int
-        L.orc2_run.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_int, ctypes.c_long]
-        L.orc2_run.restype = ctypes.c_int
+        L.orc2_step_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_int,
+                                   ctypes.c_double]
+        L.orc2_step_bc.restype = ctypes.c_int
+        L.orc2_run_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_int, ctypes.c_long,
+                                  ctypes.c_double]
+        L.orc2_run_bc.restype = ctypes.c_int
         L.orc2_moments.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]
         L.orc2_rates.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
         L.orc2_velocity_set.argtypes = [_I, _I]
@@ -57,8 +59,13 @@ def _arr(x, n=None):
 
 
 def _ok(rc):
+    if rc == -2:
+        raise ValueError("bc must be 0 (periodic) or 2 (closed box); a lid needs the box")
     if rc != 0:
         raise FloatingPointError("singular central-moment matrix")
+
+
+BC_PERIODIC, BC_BOX = 0, 2
 
 
 def velocity_set() -> np.ndarray:
@@ -105,21 +112,23 @@ def init_equilibrium(rho, ux, uy) -> np.ndarray:
     return f
 
 
-def step(f, F=(0.0, 0.0), omega=None, mode: int = 0) -> np.ndarray:
+def step(f, F=(0.0, 0.0), omega=None, mode: int = 0, bc: int = 0, uw: float = 0.0) -> np.ndarray:
+    """One step; bc 0 periodic, 2 closed box whose wall y = ny - 1/2 moves along x at uw."""
     f = _arr(f)
     _, ny, nx = f.shape
     out = np.zeros_like(f)
     om = np.ones(9) if omega is None else omega
-    _ok(lib().orc2_step(nx, ny, _p(f), _p(out), _p(_arr(F, 2)), _p(_arr(om, 9)), int(mode)))
+    _ok(lib().orc2_step_bc(nx, ny, int(bc), _p(f), _p(out), _p(_arr(F, 2)), _p(_arr(om, 9)), int(mode), float(uw)))
     return out
 
 
-def run(f, nsteps: int, F=(0.0, 0.0), omega=None, mode: int = 0) -> np.ndarray:
+def run(f, nsteps: int, F=(0.0, 0.0), omega=None, mode: int = 0, bc: int = 0, uw: float = 0.0) -> np.ndarray:
     f = _arr(f).copy()
     _, ny, nx = f.shape
     work = np.zeros_like(f)
     om = np.ones(9) if omega is None else omega
-    _ok(lib().orc2_run(nx, ny, _p(f), _p(work), _p(_arr(F, 2)), _p(_arr(om, 9)), int(mode), int(nsteps)))
+    _ok(lib().orc2_run_bc(nx, ny, int(bc), _p(f), _p(work), _p(_arr(F, 2)), _p(_arr(om, 9)), int(mode),
+                          int(nsteps), float(uw)))
     return f
 
 

@@ -200,3 +200,42 @@ def test_streaming_moves_each_population_along_its_link():
     out = O2.step(f, omega=np.ones(9))
     for a in range(9):
         assert out[a, (1 + E[a, 1]) % ny, (2 + E[a, 0]) % nx] == pytest.approx(f[a, 1, 2], abs=1e-16)
+
+
+@pytest.mark.parametrize("uw", [0.0, 0.07])
+def test_box_one_step_from_uniform_flow(uw):
+    """Closed box with a moving lid (2D cavity, Sec. 4): from a uniform equilibrium only the links
+    leaving the box change, f_opp(a)(x) = feq_a - 2 w_a rho e_ax uw / cs^2 (correction only through
+    the row y = ny, corners included)."""
+    nx, ny = 5, 4
+    u = (0.03, -0.02)
+    one = np.ones((ny, nx))
+    feq = O2.equilibrium(1.0, u)
+    w = O2.equilibrium(1.0, (0, 0))
+    got = O2.step(O2.init_equilibrium(one, u[0] * one, u[1] * one), omega=O2.rates(0.8), bc=O2.BC_BOX, uw=uw)
+    exp = np.broadcast_to(feq[:, None, None], got.shape).copy()
+    opp = [int(np.where((E == -E[a]).all(axis=1))[0][0]) for a in range(9)]
+    for y in range(ny):
+        for x in range(nx):
+            for a in range(9):
+                xd, yd = x + E[a, 0], y + E[a, 1]
+                if xd < 0 or xd >= nx or yd < 0 or yd >= ny:
+                    v = feq[a]
+                    if yd == ny:
+                        v -= 2 * w[a] * E[a, 0] * uw / CS2
+                    exp[opp[a], y, x] = v
+    assert np.max(np.abs(got - exp)) <= 1e-15
+
+
+def test_cavity_conserves_mass_and_rejects_bad_boundaries():
+    n = 6
+    one = np.ones((n, n))
+    f0 = O2.init_equilibrium(one, 0 * one, 0 * one)
+    f = O2.run(f0, 50, omega=O2.rates(0.6), bc=O2.BC_BOX, uw=0.1)
+    assert abs(f.sum() - f0.sum()) <= 1e-12 * f0.sum()
+    _, ux, _ = O2.moments(f)
+    assert ux[-1].mean() > 0.01  # the lid drags the top row
+    with pytest.raises(ValueError):
+        O2.step(f0, bc=O2.BC_PERIODIC, uw=0.1)
+    with pytest.raises(ValueError):
+        O2.step(f0, bc=1)
