@@ -284,7 +284,7 @@ FPCLBM_API const char* fpclbm_last_error(fpclbm_t h);
 
 /* ------------------------------------------------------------------------ */
 /* The 2D FPC-LBM on the D2Q9 lattice (Sec. 2 and the appendix on the 2D     */
-/* algorithm).  A separate handle: periodic nx x ny boxes, populations in the */
+/* algorithm).  A separate handle: nx x ny boxes (periodic or closed), populations in the */
 /* velocity order of Sec. 2 (e_x = 0,1,0,-1,0,1,-1,-1,1; e_y = 0,0,1,0,-1,1, */
 /* 1,-1,-1), stored as deviations from the rest weights (4/9, 1/9, 1/36) in  */
 /* the given precision, AA-pattern update in place.  Rates omega_0..omega_8  */
@@ -315,6 +315,15 @@ FPCLBM_API int fpclbm2d_set_rates(fpclbm2d_t h, const double omega[9]);
 
 /* Body force (Eq. forcing:2D).  Errors: ARG. */
 FPCLBM_API int fpclbm2d_set_force(fpclbm2d_t h, double Fx, double Fy);
+
+/* Boundary of the 2D box: FPCLBM_BC_PERIODIC (default) or FPCLBM_BC_BOX, a
+ * closed square box with half-way bounce-back at -1/2 and n - 1/2 on both
+ * axes whose wall y = ny - 1/2 moves along x at lid_ux (the 2D lid-driven
+ * cavity of Sec. 4; momentum-corrected as in fpclbm_set_wall_velocity).
+ * lid_ux must be 0 for PERIODIC.  Changing the boundary is allowed at even
+ * step counts only (the AA layout of the odd parity depends on it).
+ * Errors: ARG, STATE. */
+FPCLBM_API int fpclbm2d_set_boundary(fpclbm2d_t h, int bc, double lid_ux);
 
 /* Advance n >= 0 steps; DIVERGED if a cell saw rho <= 0 or a non-finite value.
  * Errors: ARG, STATE, CUDA, DIVERGED. */

@@ -5,8 +5,11 @@
 // buf[s * stride + cell], tensor slot s = (ex+1) + 3 (ey+1), cell = x + nx y,
 // deviations g = f - w from the rest weights w = w1(ex) w1(ey) (4/9, 1/9,
 // 1/36), AA pattern in place (even step: own slots -> opposite slot 8 - s;
-// odd step: neighbour gather / scatter), periodic in x and y.  One thread
-// per cell: 9 loads, the collision in registers, 9 stores.
+// odd step: neighbour gather / scatter), periodic in x and y or a closed
+// square box (half-way bounce-back on all four sides, the wall y = ny - 1/2
+// moving along x: the 2D lid-driven cavity of Sec. 4, handled as in 3D, see
+// cell.cuh).  One thread per cell: 9 loads, the collision in registers, 9
+// stores.
 //
 // Collision (Step 3 of the 2D appendix) in deviation form: the central
 // moments come from two 3-point passes (y lines, then x lines; see fwd3 in
@@ -41,6 +44,7 @@ struct Args2 {
     int nx, ny;
     FastDiv div_nx;
     R Fx, Fy;
+    R lid6;  // 6 x the velocity of the wall y = ny - 1/2 (closed box)
     Rates2<R> rt;
     int* flag;
 };
@@ -132,7 +136,7 @@ __device__ __forceinline__ bool collide2(R (&g)[9], const Rates2<R>& rt, R Fx, R
     return ok;
 }
 
-template <typename S, typename R, bool ODD, bool FORCE, int MODE>
+template <typename S, typename R, bool ODD, bool FORCE, int MODE, bool BOX>
 __global__ void __launch_bounds__(256) k_step2d(const Args2<R> a)
 {
     const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,33 +144,60 @@ __global__ void __launch_bounds__(256) k_step2d(const Args2<R> a)
     S* __restrict__ buf = static_cast<S*>(a.buf);
     const unsigned stride = a.stride, nx = a.nx, ny = a.ny;
     unsigned xs[3], ys[3];  // column / row offset of x - e for e = -1, 0, +1
+    bool xin[3] = {true, true, true}, yin[3] = {true, true, true};  // x - e inside the box
+    unsigned y = 0;
+    if (ODD || BOX) y = fdiv(cell, a.div_nx);
     if (ODD) {
-        const unsigned y = fdiv(cell, a.div_nx), x = cell - y * nx;
+        const unsigned x = cell - y * nx;
         xs[0] = (x + 1 == nx) ? 0u : x + 1;
         xs[1] = x;
         xs[2] = (x == 0) ? nx - 1 : x - 1;
         ys[0] = ((y + 1 == ny) ? 0u : y + 1) * nx;
         ys[1] = y * nx;
         ys[2] = ((y == 0) ? ny - 1 : y - 1) * nx;
+        if (BOX) {
+            xin[0] = x + 1 < nx;
+            xin[2] = x > 0;
+            yin[0] = y + 1 < ny;
+            yin[2] = y > 0;
+        }
     }
     R g[9];
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
-        const S* p = ODD ? buf + (size_t)(8 - s) * stride + (xs[s % 3] + ys[s / 3]) : buf + (size_t)s * stride + cell;
+        const int ix = s % 3, iy = s / 3;
+        const S* p;
+        if (!ODD || (BOX && !(xin[ix] && yin[iy])))  // even step, or bounce-back
+            p = buf + (size_t)s * stride + cell;
+        else
+            p = buf + (size_t)(8 - s) * stride + (xs[ix] + ys[iy]);
         g[s] = Store<S>::ld(p);
     }
     const bool ok = collide2<R, FORCE, MODE>(g, a.rt, a.Fx, a.Fy);
     if (!ok) atomicOr(a.flag, 1);
+    if (BOX && y + 1 == ny) {  // moving wall: -2 w_s rho e_sx u_w / cs^2 on the three e_y = +1 slots
+        R rho = R(1);
+#pragma unroll
+        for (int s = 0; s < 9; ++s) rho += g[s];
+        g[6] -= R(w1d(0) * w1d(2)) * rho * (-a.lid6);
+        g[8] -= R(w1d(2) * w1d(2)) * rho * a.lid6;
+    }
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
-        S* p = ODD ? buf + (size_t)s * stride + (xs[2 - s % 3] + ys[2 - s / 3]) : buf + (size_t)(8 - s) * stride + cell;
+        const int ix = s % 3, iy = s / 3;
+        S* p;
+        if (!ODD || (BOX && !(xin[2 - ix] && yin[2 - iy])))  // even step, or bounce-back
+            p = buf + (size_t)(8 - s) * stride + cell;
+        else
+            p = buf + (size_t)s * stride + (xs[2 - ix] + ys[2 - iy]);
         Store<S>::st(p, g[s]);
     }
 }
 
 // Deviations at the current time whatever the AA parity (as aux.cuh in 3D).
 template <typename S>
-__device__ void load2(const void* bufv, unsigned stride, int nx, int ny, int parity, unsigned cell, double g[9])
+__device__ void load2(const void* bufv, unsigned stride, int nx, int ny, int box, int parity, unsigned cell,
+                      double g[9])
 {
     const S* buf = static_cast<const S*>(bufv);
     if (parity == 0) {
@@ -176,6 +207,10 @@ __device__ void load2(const void* bufv, unsigned stride, int nx, int ny, int par
     const int y = (int)(cell / (unsigned)nx), x = (int)(cell - (unsigned)y * nx);
     for (int s = 0; s < 9; ++s) {
         const int ex = s % 3 - 1, ey = s / 3 - 1;
+        if (box && (x - ex < 0 || x - ex >= nx || y - ey < 0 || y - ey >= ny)) {  // bounce-back
+            g[s] = Store<S>::ldd(buf + (size_t)s * stride + cell);
+            continue;
+        }
         const int sx = (x - ex + nx) % nx, sy = (y - ey + ny) % ny;
         g[s] = Store<S>::ldd(buf + (size_t)(8 - s) * stride + (size_t)sx + (size_t)nx * sy);
     }
@@ -207,13 +242,13 @@ __global__ void k_init2d(void* bufv, unsigned stride, unsigned n, const double* 
 }
 
 template <typename S>
-__global__ void k_moments2d(const void* buf, unsigned stride, int nx, int ny, unsigned n, int parity, double Fx,
-                            double Fy, double* rho, double* ux, double* uy)
+__global__ void k_moments2d(const void* buf, unsigned stride, int nx, int ny, int box, unsigned n, int parity,
+                            double Fx, double Fy, double* rho, double* ux, double* uy)
 {
     const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     double g[9];
-    load2<S>(buf, stride, nx, ny, parity, c, g);
+    load2<S>(buf, stride, nx, ny, box, parity, c, g);
     double dr = 0, jx = 0, jy = 0;
     for (int s = 0; s < 9; ++s) {
         dr += g[s];
@@ -232,12 +267,13 @@ const int kEx2[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 const int kEy2[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 template <typename S>
-__global__ void k_get_pops2d(const void* buf, unsigned stride, int nx, int ny, unsigned n, int parity, double* out)
+__global__ void k_get_pops2d(const void* buf, unsigned stride, int nx, int ny, int box, unsigned n, int parity,
+                             double* out)
 {
     const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     double g[9];
-    load2<S>(buf, stride, nx, ny, parity, c, g);
+    load2<S>(buf, stride, nx, ny, box, parity, c, g);
     for (int a = 0; a < 9; ++a) {
         const int s = c_slot2[a];
         out[(size_t)a * n + c] = w1d(s % 3) * w1d(s / 3) + g[s];
@@ -256,11 +292,11 @@ __global__ void k_set_pops2d(void* bufv, unsigned stride, unsigned n, const doub
     }
 }
 
-template <typename S, typename R>
+template <typename S, typename R, bool BOX>
 cudaError_t step2d_go(int odd, int force, int mode, const Args2<R>& a, cudaStream_t st)
 {
     const unsigned grid = (a.ncells + 255) / 256;
-#define FPC2_K(O, FO, M) k_step2d<S, R, O, FO, M><<<grid, 256, 0, st>>>(a)
+#define FPC2_K(O, FO, M) k_step2d<S, R, O, FO, M, BOX><<<grid, 256, 0, st>>>(a)
     if (odd) {
         if (force) { if (mode == MODE_EQ) FPC2_K(true, true, MODE_EQ); else FPC2_K(true, true, MODE_FP); }
         else { if (mode == MODE_EQ) FPC2_K(true, false, MODE_EQ); else FPC2_K(true, false, MODE_FP); }
@@ -289,6 +325,8 @@ struct fpclbm2d {
     double omega[9];
     double F[2] = {0, 0};
     int diffusion = FPCLBM_DIFF_FP;
+    int bc = FPCLBM_BC_PERIODIC;
+    double lid = 0;
     long long steps = 0;
     bool initialized = false;
     cudaGraphExec_t graph = nullptr;
@@ -326,6 +364,7 @@ Args2<R> args_of(const fpclbm2d* h)
     a.div_nx = make_fastdiv((unsigned)h->nx);
     a.Fx = (R)h->F[0];
     a.Fy = (R)h->F[1];
+    a.lid6 = (R)(6.0 * h->lid);
     for (int j = 0; j < 9; ++j) {
         a.rt.om[j] = (R)h->omega[j];
         a.rt.keep[j] = (R)(1.0 - h->omega[j]);
@@ -339,12 +378,16 @@ cudaError_t one_step2(fpclbm2d* h, long long t, cudaStream_t st)
 {
     const int odd = (int)(t & 1), force = h->F[0] != 0.0 || h->F[1] != 0.0;
     const int mode = h->diffusion == FPCLBM_DIFF_EQUILIBRIUM ? MODE_EQ : MODE_FP;
+    const bool box = h->bc == FPCLBM_BC_BOX;
+#define FPC2_GO(S, R) (box ? step2d_go<S, R, true>(odd, force, mode, args_of<R>(h), st) \
+                           : step2d_go<S, R, false>(odd, force, mode, args_of<R>(h), st))
     switch (h->precision) {
-        case FPCLBM_FP64: return step2d_go<double, double>(odd, force, mode, args_of<double>(h), st);
-        case FPCLBM_FP32: return step2d_go<float, float>(odd, force, mode, args_of<float>(h), st);
-        case FPCLBM_FP32_STORE_FP16: return step2d_go<__half, float>(odd, force, mode, args_of<float>(h), st);
-        case FPCLBM_FP32_STORE_BF16: return step2d_go<__nv_bfloat16, float>(odd, force, mode, args_of<float>(h), st);
+        case FPCLBM_FP64: return FPC2_GO(double, double);
+        case FPCLBM_FP32: return FPC2_GO(float, float);
+        case FPCLBM_FP32_STORE_FP16: return FPC2_GO(__half, float);
+        case FPCLBM_FP32_STORE_BF16: return FPC2_GO(__nv_bfloat16, float);
     }
+#undef FPC2_GO
     return cudaErrorInvalidValue;
 }
 
@@ -504,6 +547,21 @@ int fpclbm2d_set_force(fpclbm2d_t h, double Fx, double Fy)
     return FPCLBM_OK;
 }
 
+int fpclbm2d_set_boundary(fpclbm2d_t h, int bc, double lid_ux)
+{
+    if (!h) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    if (bc != FPCLBM_BC_PERIODIC && bc != FPCLBM_BC_BOX) return fail2(h, FPCLBM_ERR_ARG, "2D boundary must be PERIODIC or BOX");
+    if (!std::isfinite(lid_ux) || (bc == FPCLBM_BC_PERIODIC && lid_ux != 0.0))
+        return fail2(h, FPCLBM_ERR_ARG, "lid velocity must be finite and needs the closed box");
+    if (bc != h->bc && h->initialized && (h->steps & 1))
+        return fail2(h, FPCLBM_ERR_STATE, "change the boundary at an even step count");
+    h->bc = bc;
+    h->lid = lid_ux;
+    h->graph_valid = false;
+    return FPCLBM_OK;
+}
+
 int fpclbm2d_step(fpclbm2d_t h, long long n)
 {
     if (!h) return FPCLBM_ERR_ARG;
@@ -566,10 +624,10 @@ int fpclbm2d_moments(fpclbm2d_t h, double* rho, double* ux, double* uy, int on_d
     const unsigned blocks = (h->ncells + 255) / 256;
     const int parity = (int)(h->steps & 1);
     switch (h->precision) {
-        case FPCLBM_FP64: k_moments2d<double><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
-        case FPCLBM_FP32: k_moments2d<float><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
-        case FPCLBM_FP32_STORE_FP16: k_moments2d<__half><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
-        default: k_moments2d<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
+        case FPCLBM_FP64: k_moments2d<double><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
+        case FPCLBM_FP32: k_moments2d<float><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
+        case FPCLBM_FP32_STORE_FP16: k_moments2d<__half><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
+        default: k_moments2d<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, h->F[0], h->F[1], o[0], o[1], o[2]); break;
     }
     cudaError_t e = cudaGetLastError();
     double* host[3] = {rho, ux, uy};
@@ -597,10 +655,10 @@ int fpclbm2d_get_populations(fpclbm2d_t h, double* f)
     const unsigned blocks = (h->ncells + 255) / 256;
     const int parity = (int)(h->steps & 1);
     switch (h->precision) {
-        case FPCLBM_FP64: k_get_pops2d<double><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, d); break;
-        case FPCLBM_FP32: k_get_pops2d<float><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, d); break;
-        case FPCLBM_FP32_STORE_FP16: k_get_pops2d<__half><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, d); break;
-        default: k_get_pops2d<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->ncells, parity, d); break;
+        case FPCLBM_FP64: k_get_pops2d<double><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, d); break;
+        case FPCLBM_FP32: k_get_pops2d<float><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, d); break;
+        case FPCLBM_FP32_STORE_FP16: k_get_pops2d<__half><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, d); break;
+        default: k_get_pops2d<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>(h->d_pop, h->stride, h->nx, h->ny, h->bc == FPCLBM_BC_BOX, h->ncells, parity, d); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);

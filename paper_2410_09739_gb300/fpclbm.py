@@ -53,7 +53,7 @@ EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fp
             "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc", "fpclbm_closure_sample",
             "fpclbm_closure_train", "fpclbm_closure_grad",
             "fpclbm2d_create", "fpclbm2d_init_fields", "fpclbm2d_set_params", "fpclbm2d_set_rates",
-            "fpclbm2d_set_force", "fpclbm2d_step", "fpclbm2d_moments", "fpclbm2d_get_populations",
+            "fpclbm2d_set_force", "fpclbm2d_set_boundary", "fpclbm2d_step", "fpclbm2d_moments", "fpclbm2d_get_populations",
             "fpclbm2d_set_populations", "fpclbm2d_destroy", "fpclbm2d_last_error")
 
 
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
     L.fpclbm2d_set_params.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.fpclbm2d_set_rates.argtypes = [_P, _D]
     L.fpclbm2d_set_force.argtypes = [_P, ctypes.c_double, ctypes.c_double]
+    L.fpclbm2d_set_boundary.argtypes = [_P, ctypes.c_int, ctypes.c_double]
     L.fpclbm2d_step.argtypes = [_P, ctypes.c_longlong]
     L.fpclbm2d_moments.argtypes = [_P, _P, _P, _P, ctypes.c_int]
     L.fpclbm2d_get_populations.argtypes = [_P, _P]
@@ -426,6 +427,10 @@ def fpclbm2d_set_force(h, Fx: float, Fy: float):
     return _check2(h, load().fpclbm2d_set_force(h, float(Fx), float(Fy)))
 
 
+def fpclbm2d_set_boundary(h, bc: int, lid_ux: float = 0.0):
+    return _check2(h, load().fpclbm2d_set_boundary(h, int(bc), float(lid_ux)))
+
+
 def fpclbm2d_step(h, n: int):
     return _check2(h, load().fpclbm2d_step(h, int(n)))
 
@@ -492,6 +497,9 @@ class Lattice2D:
 
     def set_force(self, Fx, Fy=0.0):
         return fpclbm2d_set_force(self.h, Fx, Fy)
+
+    def set_boundary(self, bc, lid_ux=0.0):
+        return fpclbm2d_set_boundary(self.h, bc, lid_ux)
 
     def step(self, n: int = 1):
         return fpclbm2d_step(self.h, n)

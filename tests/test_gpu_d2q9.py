@@ -126,3 +126,52 @@ def test_errors():
         with pytest.raises(F.FpclbmError) as e:
             lat.step(1)
         assert e.value.code == F.FPCLBM_ERR_DIVERGED
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (5, 4), (33, 7), (64, 9)])
+@pytest.mark.parametrize("mode", [F.FPCLBM_DIFF_FP, F.FPCLBM_DIFF_EQUILIBRIUM])
+@pytest.mark.parametrize("lid", [0.0, 0.06])
+def test_fp64_closed_box_matches_oracle(shape, mode, lid):
+    """2D lid-driven cavity walls (bounce-back on all four sides, moving wall y = ny - 1/2)."""
+    nx, ny = shape
+    f0 = near_eq(nx, ny, 500 + nx + ny + mode)
+    rng = np.random.default_rng(nx * ny)
+    om = rng.uniform(0.6, 1.6, 9)
+    om[5] = om[4]
+    Fv = (1e-4, -2e-4)
+    with F.Lattice2D(nx, ny, "fp64") as lat:
+        lat.set_params(1.0, 0.0, 0.0, mode)
+        lat.set_rates(om)
+        lat.set_force(*Fv)
+        lat.set_boundary(F.FPCLBM_BC_BOX, lid)
+        lat.set_populations(f0)
+        ref = f0
+        for n in (1, 2, 5, 40):
+            lat.step(n)
+            ref = O2.run(ref, n, F=Fv, omega=om, mode=mode, bc=O2.BC_BOX, uw=lid)
+            assert rel(lat.get_populations(), ref) <= 1e-12 * (n + 1), n
+            r, u, v = lat.moments()
+            r2, u2, v2 = O2.moments(ref, Fv)
+            assert np.max(np.abs(u - u2)) <= 1e-12
+
+
+def test_closed_box_fp32_and_errors():
+    n = 48
+    one = np.ones((n, n))
+    with F.Lattice2D(n, n, "fp32") as lat:
+        with pytest.raises(F.FpclbmError):
+            lat.set_boundary(F.FPCLBM_BC_PERIODIC, 0.1)  # a lid needs the closed box
+        with pytest.raises(F.FpclbmError):
+            lat.set_boundary(F.FPCLBM_BC_WALLS_Y)
+        lat.set_boundary(F.FPCLBM_BC_BOX, 0.08)
+        lat.set_params(0.56)
+        lat.init_fields(one, 0 * one, 0 * one)
+        f0 = lat.get_populations()
+        lat.step(7)
+        got = lat.get_populations()
+        with pytest.raises(F.FpclbmError) as e:
+            lat.set_boundary(F.FPCLBM_BC_PERIODIC)  # odd step count
+        assert e.value.code == F.FPCLBM_ERR_STATE
+    ref = O2.run(f0, 7, omega=O2.rates(0.56), bc=O2.BC_BOX, uw=0.08)
+    assert np.max(np.abs(got - ref)) <= 7e-6
+    assert abs(got.sum() - f0.sum()) <= 1e-4 * f0.sum()

@@ -53,3 +53,26 @@ def test_full_channel_perturbation_crosses_the_centre_plane():
     du, dv, dw = CH.perturbation(nx, ny, nz, ny, 1.0, full=True)
     assert np.max(np.abs(dv[:, ny // 2, :])) > 0.3  # v' does not vanish at the centre
     assert np.max(np.abs(du[:, 0, :])) < 0.06 and np.max(np.abs(du[:, -1, :])) < 0.06
+
+
+def test_cavity2d_vortex_centres_of_a_synthetic_stream_function():
+    from paper_2410_09739_gb300 import cavity2d_study as C2
+    L = 200
+    c = (np.arange(L) + 0.5) / L
+    x, y = np.meshgrid(c, c)
+
+    def well(x0, y0, a, s):
+        return a * np.exp(-((x - x0) ** 2 + (y - y0) ** 2) / s ** 2)
+
+    psi = well(0.531, 0.565, -0.1, 0.2) + well(0.864, 0.112, 1e-3, 0.03) + well(0.083, 0.077, 1e-4, 0.02)
+    cen = C2.vortex_centres(psi)
+    assert abs(cen["PV"][0] - 0.531) < 2e-3 and abs(cen["PV"][1] - 0.565) < 2e-3
+    assert abs(cen["BR1"][0] - 0.864) < 3e-3 and abs(cen["BR1"][1] - 0.112) < 3e-3
+    assert abs(cen["BL"][0] - 0.083) < 3e-3 and abs(cen["BL"][1] - 0.077) < 3e-3
+
+
+def test_cavity2d_stream_function_integrates_u():
+    from paper_2410_09739_gb300 import cavity2d_study as C2
+    ux = np.ones((10, 3))
+    psi = C2.stream_function(ux)
+    assert np.allclose(psi[:, 0], np.arange(10) + 0.5)
