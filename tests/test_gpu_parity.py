@@ -323,22 +323,31 @@ def test_full_size_channel_bf16_sampled():
         _check_sampled(lat, (nx, ny, nz), 1, (Fx, 0, 0), O.rates(tau), 2.0 ** -8, seed=2)
 
 
-def test_fp32_velocity_error_after_1000_steps():
+def test_velocity_error_after_1000_steps():
     """Stated bound: FP32 path within 1e-5 (relative to u0) in velocity after 1000 steps of the
-    256^3 Re = 1600 TGV, against the FP64 GPU path (itself at oracle parity)."""
+    256^3 Re = 1600 TGV, against the FP64 GPU path (itself at oracle parity).  The 16-bit storage
+    variants have no stated bound; their errors are measured and printed (max and RMS of |du|/u0)
+    and checked only against loose ceilings (FP16 5e-2, BF16 2.5e-1) that catch a broken path."""
     torch = pytest.importorskip("torch")
     n, u0, steps = 256, 0.05, 1000
     nu = W.tgv_viscosity(n, u0, 1600.0)
     tau = 3 * nu + 0.5
     rho, ux, uy, uz = W.tgv(n, u0)
     outs = {}
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp16", "bf16"):
         with make(n, n, n, prec, tau=tau) as lat:
             lat.init_fields(rho, ux, uy, uz)
             lat.step(steps)
             dev = [torch.empty(n ** 3, dtype=torch.float64, device="cuda") for _ in range(4)]
             F.fpclbm_moments(lat.h, *dev, on_device=1)
             outs[prec] = dev
-    err = max(float((outs["fp32"][q] - outs["fp64"][q]).abs().max()) for q in (1, 2, 3)) / u0
-    print("fp32 max |du|/u0 after %d steps: %.3e" % (steps, err))
-    assert err <= 1e-5
+    errs = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        d = [outs[prec][q] - outs["fp64"][q] for q in (1, 2, 3)]
+        mx = max(float(x.abs().max()) for x in d) / u0
+        rms = float(torch.sqrt(sum((x * x).mean() for x in d) / 3)) / u0
+        errs[prec] = (mx, rms)
+        print("%s storage, max |du|/u0 after %d steps: %.3e (rms %.3e)" % (prec, steps, mx, rms))
+    assert errs["fp32"][0] <= 1e-5
+    assert errs["fp16"][0] <= 5e-2
+    assert errs["bf16"][0] <= 2.5e-1
