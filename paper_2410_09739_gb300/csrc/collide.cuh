@@ -25,6 +25,11 @@
 // Readings: first-order moments enter attractors and sources as 0; sources
 // use pre-collision moments; attractors of orders 4-6 use post-collision
 // lower moments; kappa^Mv_122 carries Pi_110 Pi_012 (continuous form).
+// In the modes *_R1 (rates of orders 3-6 equal to 1, no force) the moments of
+// orders 3-6 are set to their attractors; the third- and fifth-order
+// attractors vanish there (they are built from odd moments that are zero
+// after the collision), and the unused pre-collision moments of those orders
+// drop out of the forward transform.
 #pragma once
 #include "common.cuh"
 #include "pair.cuh"
@@ -107,6 +112,8 @@ template <typename R, bool FORCE, int MODE>
 __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R Fx, R Fy, R Fz, R om4, R om5, R om6,
                                              R om8, R om9, const float* closure, R c2 = R(0))
 {
+    constexpr bool R1 = r1_mode(MODE);
+    static_assert(!(R1 && FORCE), "the unit-rate modes carry no body force");
     // ---- Step 7 and the first pass (z lines), sharing the line sums ----
     R S[9], Dz[9], Pz[9];
 #pragma unroll
@@ -251,6 +258,11 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     }
 
     // order 3 (attractors 0): pairs (120,102), (210,012), (201,021), and 111
+    if constexpr (R1) {
+        FPC_D(1, 2, 0) = FPC_D(1, 0, 2) = FPC_D(2, 1, 0) = R(0);
+        FPC_D(0, 1, 2) = FPC_D(2, 0, 1) = FPC_D(0, 2, 1) = R(0);
+        FPC_D(1, 1, 1) = R(0);
+    } else {
 #define FPC_PAIR3(A, B, sa, sb, j)                                                      \
     {                                                                                   \
         const R ys = A + B, ym = A - B;                                                 \
@@ -268,6 +280,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
 #undef FPC_PAIR3
     FPC_D(1, 1, 1) = rt.keep[16] * FPC_D(1, 1, 1);
     if (FORCE) FPC_D(1, 1, 1) = fmaR(rt.src[16], s111, FPC_D(1, 1, 1));
+    }
 
     // sources of order 5 from the pre-collision fourth moments
     R s122 = 0, s212 = 0, s221 = 0;
@@ -285,7 +298,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     // order 4: groups 4s1, 4d1, 4d2 and 211, 121, 112
     {
         R A220, A202, A022, A211, A121, A112;
-        if constexpr (MODE == MODE_EQ) {
+        if constexpr (eq_mode(MODE)) {
             A220 = A202 = A022 = ninth * drho;  // cs^4 rho - 1/9
             A211 = A121 = A112 = R(0);
         } else {
@@ -297,6 +310,14 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
             A121 = fmaR(third + pb, o101, R(2) * o110 * o011) * inv_rho;
             A112 = fmaR(third + pc, o110, R(2) * o011 * o101) * inv_rho;
         }
+        if constexpr (R1) {
+            FPC_D(2, 2, 0) = A220;
+            FPC_D(2, 0, 2) = A202;
+            FPC_D(0, 2, 2) = A022;
+            FPC_D(2, 1, 1) = A211;
+            FPC_D(1, 2, 1) = A121;
+            FPC_D(1, 1, 2) = A112;
+        } else {
         const R d220 = FPC_D(2, 2, 0), d202 = FPC_D(2, 0, 2), d022 = FPC_D(0, 2, 2);
         const R y4s = (d220 + d202) + d022, y4d1 = (d220 + d202) - d022, y4d2 = d220 - d202;
         const R a4s = (A220 + A202) + A022, a4d1 = (A220 + A202) - A022, a4d2 = A220 - A202;
@@ -322,6 +343,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
         FPC_D(2, 1, 1) = t211;
         FPC_D(1, 2, 1) = t121;
         FPC_D(1, 1, 2) = t112;
+        }
     }
 
     // source of order 6 from the pre-collision fifth moments
@@ -329,9 +351,11 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     if (FORCE) s222 = R(2) * ((fx * FPC_D(1, 2, 2) + fy * FPC_D(2, 1, 2)) + fz * FPC_D(2, 2, 1));
 
     // order 5: attractors from post-collision second and third moments
-    {
+    if constexpr (R1) {
+        FPC_D(1, 2, 2) = FPC_D(2, 1, 2) = FPC_D(2, 2, 1) = R(0);
+    } else {
         R A122 = R(0), A212 = R(0), A221 = R(0);
-        if constexpr (MODE != MODE_EQ) {
+        if constexpr (!eq_mode(MODE)) {
             const R K200 = third + pa, K020 = third + pb, K002 = third + pc;
             const R k111 = FPC_D(1, 1, 1);
             const R c = R(0.4) * inv_rho;
@@ -358,7 +382,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     // order 6: attractor from post-collision second and fourth moments
     {
         R A222;
-        if constexpr (MODE == MODE_EQ) {
+        if constexpr (eq_mode(MODE)) {
             A222 = R(1.0 / 27.0) * drho;  // cs^6 rho - 1/27
         } else {
             const R q220 = FPC_D(2, 2, 0), q202 = FPC_D(2, 0, 2), q022 = FPC_D(0, 2, 2);
@@ -367,9 +391,13 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
             t = fmaR(R(4), fmaR(o110, FPC_D(1, 1, 2), fmaR(o101, FPC_D(1, 2, 1), o011 * FPC_D(2, 1, 1))), t);
             A222 = (t - ninth * drho) * (third * inv_rho);
         }
-        R t222 = fmaR(rt.om[26], A222, rt.keep[26] * FPC_D(2, 2, 2));
-        if (FORCE) t222 = fmaR(rt.src[26], s222, t222);
-        FPC_D(2, 2, 2) = t222;
+        if constexpr (R1) {
+            FPC_D(2, 2, 2) = A222;
+        } else {
+            R t222 = fmaR(rt.om[26], A222, rt.keep[26] * FPC_D(2, 2, 2));
+            if (FORCE) t222 = fmaR(rt.src[26], s222, t222);
+            FPC_D(2, 2, 2) = t222;
+        }
     }
 
     // ---- Steps 4+5: back to populations (passes in reverse order) ----

@@ -17,8 +17,18 @@ namespace fpc {
 
 // Attractor modes of the collision: FP diffusion tensor, Maxwellian (MCM),
 // FP with the learned shear-rate correction, FP with the Smagorinsky eddy
-// viscosity (van Driest damped) in the shear rates.
-enum { MODE_FP = 0, MODE_EQ = 1, MODE_LEARNED = 2, MODE_SMAG = 3 };
+// viscosity (van Driest damped) in the shear rates.  MODE_FP_R1 and
+// MODE_EQ_R1 are the FP and MCM modes in the paper's default setting, every
+// rate of order >= 3 equal to 1 and no body force: the post-collision moments
+// of orders 3-6 are then their attractors (kappa + 1 (kappa^Mv - kappa) =
+// kappa^Mv, no source), so the pre-collision moments of those orders are not
+// formed at all.
+enum { MODE_FP = 0, MODE_EQ = 1, MODE_LEARNED = 2, MODE_SMAG = 3, MODE_FP_R1 = 4, MODE_EQ_R1 = 5 };
+
+// FP or MCM attractors with the full register-cap / pipelined / paired variant set.
+__host__ __device__ constexpr bool plain_mode(int m) { return m == MODE_FP || m == MODE_EQ || m == MODE_FP_R1 || m == MODE_EQ_R1; }
+__host__ __device__ constexpr bool eq_mode(int m) { return m == MODE_EQ || m == MODE_EQ_R1; }
+__host__ __device__ constexpr bool r1_mode(int m) { return m == MODE_FP_R1 || m == MODE_EQ_R1; }
 
 // Boundary kinds of the step kernel: periodic box; half-way bounce-back walls
 // at y = -1/2 and ny - 1/2 (x, z periodic); the same with the wall at

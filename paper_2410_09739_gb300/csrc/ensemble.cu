@@ -97,46 +97,62 @@ static cudaError_t go(const EnsArgs& a, int block, int minb, int grid, int varia
     return cudaGetLastError();
 }
 
+template <int MODE>
+static cudaError_t go_mode(int odd, int force, const EnsArgs& a, int block, int minb, int grid, int variant,
+                           cudaStream_t st)
+{
+    if constexpr (r1_mode(MODE)) {  // unit rates of orders >= 3: no body force by construction
+        if (force) return cudaErrorInvalidValue;
+        return odd ? go<true, false, MODE>(a, block, minb, grid, variant, st)
+                   : go<false, false, MODE>(a, block, minb, grid, variant, st);
+    } else {
+        if (odd) return force ? go<true, true, MODE>(a, block, minb, grid, variant, st)
+                              : go<true, false, MODE>(a, block, minb, grid, variant, st);
+        return force ? go<false, true, MODE>(a, block, minb, grid, variant, st)
+                     : go<false, false, MODE>(a, block, minb, grid, variant, st);
+    }
+}
+
 cudaError_t launch_ens_step(int odd, int force, int mode, const EnsArgs& a, int block, int minb, int grid,
                             int variant, cudaStream_t st)
 {
     if (grid <= 0 || block <= 0 || block > 256 || a.tile_cells % block != 0) return cudaErrorInvalidValue;
-#define FPC_ENS(O, Fo, M) return go<O, Fo, M>(a, block, minb, grid, variant, st)
-    if (mode == MODE_FP) {
-        if (odd) { if (force) FPC_ENS(true, true, MODE_FP); FPC_ENS(true, false, MODE_FP); }
-        if (force) FPC_ENS(false, true, MODE_FP);
-        FPC_ENS(false, false, MODE_FP);
+    switch (mode) {
+        case MODE_FP: return go_mode<MODE_FP>(odd, force, a, block, minb, grid, variant, st);
+        case MODE_EQ: return go_mode<MODE_EQ>(odd, force, a, block, minb, grid, variant, st);
+        case MODE_FP_R1: return go_mode<MODE_FP_R1>(odd, force, a, block, minb, grid, variant, st);
+        case MODE_EQ_R1: return go_mode<MODE_EQ_R1>(odd, force, a, block, minb, grid, variant, st);
     }
-    if (mode == MODE_EQ) {
-        if (odd) { if (force) FPC_ENS(true, true, MODE_EQ); FPC_ENS(true, false, MODE_EQ); }
-        if (force) FPC_ENS(false, true, MODE_EQ);
-        FPC_ENS(false, false, MODE_EQ);
-    }
-#undef FPC_ENS
     return cudaErrorInvalidValue;
 }
 
-int ens_max_blocks_per_sm(int block, int minb, int mode, int variant)
+// Resident blocks per SM of the even-step kernel of the variant that launch_ens_step runs.
+template <int MODE>
+static int ens_occupancy(int block, int minb, int variant)
 {
     int n = 0;
     cudaError_t e;
-    if (variant == 2 && minb == 3)
-        e = mode == MODE_EQ ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_EQ, 3>, block, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_FP, 3>, block, 0);
-    else if (variant == 2)
-        e = mode == MODE_EQ ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_EQ, 4>, block, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE_FP, 4>, block, 0);
-    else if (mode == MODE_EQ)
-        e = minb == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_EQ, 3>, block, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_EQ, 2>, block, 0);
+    if (variant == 2)
+        e = minb == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE, 3>, block, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_pair<false, false, MODE, 4>, block, 0);
     else
-        e = minb == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_FP, 3>, block, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE_FP, 2>, block, 0);
+        e = minb == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE, 3>, block, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<false, false, MODE, 2>, block, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     return n > 0 ? n : 1;
+}
+
+int ens_max_blocks_per_sm(int block, int minb, int mode, int variant)
+{
+    switch (mode) {
+        case MODE_EQ: return ens_occupancy<MODE_EQ>(block, minb, variant);
+        case MODE_FP_R1: return ens_occupancy<MODE_FP_R1>(block, minb, variant);
+        case MODE_EQ_R1: return ens_occupancy<MODE_EQ_R1>(block, minb, variant);
+    }
+    return ens_occupancy<MODE_FP>(block, minb, variant);
 }
 
 }  // namespace fpc

@@ -193,15 +193,21 @@ BoxGeom geom_of(const fpclbm* h, const Box& b)
     return g;
 }
 
+bool has_force(const fpclbm* h) { return h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0; }
+
+// Collision mode of the step kernel.  A box or ensemble in the FP or MCM mode whose rates of
+// orders 3-6 (Step 3 indices 10..26) are all exactly 1 and that carries no body force takes
+// the unit-rate variant, which never forms the pre-collision moments of those orders.
 int mode_of(const fpclbm* h)
 {
-    if (h->diffusion == FPCLBM_DIFF_EQUILIBRIUM) return MODE_EQ;
     if (h->diffusion == FPCLBM_DIFF_FP_LEARNED) return MODE_LEARNED;
     if (h->diffusion == FPCLBM_DIFF_FP_SMAGORINSKY) return MODE_SMAG;
-    return MODE_FP;
+    const int m = h->diffusion == FPCLBM_DIFF_EQUILIBRIUM ? MODE_EQ : MODE_FP;
+    if (has_force(h)) return m;
+    for (int j = 10; j < 27; ++j)
+        if (h->omega[j] != 1.0) return m;
+    return m == MODE_EQ ? MODE_EQ_R1 : MODE_FP_R1;
 }
-
-bool has_force(const fpclbm* h) { return h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0; }
 
 // Boundary kind of the step kernel: a channel whose upper wall moves takes the
 // moving-wall variant; a closed box always does (its lid may rest).
@@ -378,8 +384,8 @@ int autotune(fpclbm* h)
     // same on periodic and channel boxes with 4- or 8-byte storage (cp.async moves >= 4 bytes)
     const int kb = kernel_bc(h), md = mode_of(h);
     const bool fixed_walls = bc_fixed(kb);
-    const bool fp32_math = h->precision != FPCLBM_FP64 && (md == MODE_FP || md == MODE_EQ);
-    const bool pipe_ok = elem_size(h->precision) >= 4 && (md == MODE_FP || md == MODE_EQ) &&
+    const bool fp32_math = h->precision != FPCLBM_FP64 && plain_mode(md);
+    const bool pipe_ok = elem_size(h->precision) >= 4 && plain_mode(md) &&
                          (kb == BC_PERIODIC || kb == BC_WALLS_Y);
     // paired variant (two cells per thread, packed fp32): fp32 arithmetic, periodic and channel
     const bool pair_ok = fp32_math && (kb == BC_PERIODIC || kb == BC_WALLS_Y);
@@ -669,7 +675,9 @@ int fpclbm_set_rates(fpclbm_t h, const double omega[27])
     if (h->ensemble) return fail(h, FPCLBM_ERR_ARG, "set_rates is for single boxes");
     std::string why;
     if (!rates_valid(omega, why)) return fail(h, FPCLBM_ERR_PARAM, why);
+    const int md = mode_of(h);
     std::memcpy(h->omega, omega, sizeof(double) * 27);
+    if (mode_of(h) != md) h->tuned = false;  // another kernel family: tune it
     h->graph_valid = false;
     h->smag_dirty = true;
     return FPCLBM_OK;

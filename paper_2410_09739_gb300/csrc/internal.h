@@ -18,7 +18,7 @@ struct StepLaunch {
 
 // One time step of a single box.  odd selects the AA-pattern parity (0: own
 // slots, 1: neighbour slots), bc the boundary kind (BC_*), force the source
-// terms, mode MODE_FP / MODE_EQ / MODE_LEARNED.
+// terms, mode one of the MODE_* collision modes (common.cuh).
 cudaError_t launch_step(int precision, int odd, int bc, int force, int mode, const StepArgs<double>& a64,
                         const StepArgs<float>& a32, const StepLaunch& cfg, cudaStream_t st);
 

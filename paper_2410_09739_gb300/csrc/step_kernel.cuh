@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(128, MINB) k_step_pipe(const StepArgs<R> a, un
 {
     static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async moves 4, 8 or 16 bytes");
     static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y, "periodic or channel boxes only");
-    static_assert(MODE == MODE_FP || MODE == MODE_EQ, "FP and MCM modes only");
+    static_assert(plain_mode(MODE), "FP and MCM modes only");
     extern __shared__ __align__(16) unsigned char fpc_smem[];
     S* sm = reinterpret_cast<S*>(fpc_smem);
     const unsigned T = blockDim.x, tid = threadIdx.x;
@@ -202,12 +202,12 @@ cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st
 {
     // paired variant: fp32 arithmetic, FP and MCM modes, periodic and channel boxes, one register
     // cap (4 blocks of 128 threads: 128 registers hold two cells without spilling)
-    if constexpr (sizeof(R) == 4 && (MODE == MODE_FP || MODE == MODE_EQ) && BC <= BC_WALLS_Y && MINB == 2) {
+    if constexpr (sizeof(R) == 4 && plain_mode(MODE) && BC <= BC_WALLS_Y && MINB == 2) {
         if (cfg.pipe == 2) return step_go_pair<S, ODD, BC, FORCE, MODE, MINB>(a, st);
     }
     // the pipelined variant retires tail lanes early, so it never runs the warp-collective
     // learned mode; it exists for the FP and MCM modes of periodic and channel boxes
-    if constexpr (sizeof(S) >= 4 && (MODE == MODE_FP || MODE == MODE_EQ) && BC <= BC_WALLS_Y) {
+    if constexpr (sizeof(S) >= 4 && plain_mode(MODE) && BC <= BC_WALLS_Y) {
         if (cfg.pipe == 1) return step_go_pipe<S, R, ODD, BC, FORCE, MODE, MINB>(a, st);
     }
     const int block = cfg.block > 0 ? cfg.block : 256;
@@ -223,7 +223,7 @@ cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st
 template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE>
 cudaError_t step_by_minb(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
-    constexpr bool fp32_capped = sizeof(R) == 4 && (MODE == MODE_FP || MODE == MODE_EQ);
+    constexpr bool fp32_capped = sizeof(R) == 4 && plain_mode(MODE);
     constexpr bool fp32_learned = sizeof(R) == 4 && MODE == MODE_LEARNED && bc_fixed(BC);
     if constexpr (fp32_capped) {
         if (cfg.minb == 3) return step_go<S, R, ODD, BC, FORCE, MODE, 3>(a, cfg, st);
@@ -243,6 +243,12 @@ cudaError_t step_by_mode(int mode, const StepArgs<R>& a, const StepLaunch& cfg, 
     switch (mode) {
         case MODE_FP: return step_by_minb<S, R, ODD, BC, FORCE, MODE_FP>(a, cfg, st);
         case MODE_EQ: return step_by_minb<S, R, ODD, BC, FORCE, MODE_EQ>(a, cfg, st);
+        case MODE_FP_R1:  // unit rates of orders >= 3 without body force
+            if constexpr (!FORCE) return step_by_minb<S, R, ODD, BC, FORCE, MODE_FP_R1>(a, cfg, st);
+            break;
+        case MODE_EQ_R1:
+            if constexpr (!FORCE) return step_by_minb<S, R, ODD, BC, FORCE, MODE_EQ_R1>(a, cfg, st);
+            break;
         case MODE_LEARNED:  // periodic and channel boxes (the closure's training data come from them)
             if constexpr (BC == BC_PERIODIC || BC == BC_WALLS_Y)
                 return step_by_minb<S, R, ODD, BC, FORCE, MODE_LEARNED>(a, cfg, st);

@@ -52,6 +52,35 @@ def test_each_box_matches_oracle_and_single_box(monkeypatch, nsteps, launch):
             assert np.array_equal(one.get_populations(), mine)
 
 
+@pytest.mark.parametrize("launch", ["", "128:4:2"])
+def test_generic_rates_and_force_match_oracle_and_single_box(monkeypatch, launch):
+    """Rates of orders >= 3 other than 1 (drift 0.2) and a body force: the general collision kernels
+    (the default rates without force take the unit-rate kernels)."""
+    monkeypatch.setenv("FPCLBM_LAUNCH", launch)
+    fs = fields(77)
+    Fv = (2e-5, -1e-5, 1.5e-5)
+    nsteps = 5
+    with F.Lattice.ensemble(DIMS, TAUS, "fp32") as ens:
+        ens.set_params(1.0, 0.2)
+        ens.set_force(*Fv)
+        ens.init_fields(*concat(fs))
+        ens.step(nsteps)
+        got = ens.get_populations()
+    c0 = 0
+    for (nx, ny, nz), tau, fld in zip(DIMS, TAUS, fs):
+        n = nx * ny * nz
+        mine = got[:, c0:c0 + n].reshape(27, nz, ny, nx)
+        c0 += n
+        ref = O.run(O.init_equilibrium(*fld), nsteps, F=Fv, omega=O.rates(tau, 0.2))
+        assert np.max(np.abs(mine - ref)) <= 1e-6 * nsteps
+        with F.Lattice(nx, ny, nz, "fp32") as one:
+            one.set_params(tau, 0.2)
+            one.set_force(*Fv)
+            one.init_fields(*fld)
+            one.step(nsteps)
+            assert np.array_equal(one.get_populations(), mine)
+
+
 def test_ensemble_mcm_mode_and_diagnostics():
     fs = fields(3)
     with F.Lattice.ensemble(DIMS, TAUS, "fp32") as ens:

@@ -86,6 +86,29 @@ def test_one_step_fp64_random_populations(shape, bc, force, mode):
     assert rel(got, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("shape", [(3, 3, 3), (17, 9, 5)])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_one_step_fp64_unit_high_rates(shape, bc, mode):
+    """Rates of orders 3-6 exactly 1 and no force (the paper's default) select the unit-rate
+    kernels, which set those moments straight to their attractors; random populations far from
+    equilibrium, random shear and bulk rates, every boundary kind (closed box with a moving lid)."""
+    nx, ny, nz = shape
+    seed = 500 + nx + bc * 7 + mode
+    f0 = W.random_populations(nx * ny * nz, seed).reshape(27, nz, ny, nx)
+    om = random_rates(seed)
+    om[10:] = 1.0
+    uw = 0.03 if bc == 2 else 0.0
+    with make(nx, ny, nz, "fp64", bc, omega=om, mode=mode) as lat:
+        if bc == 2:
+            lat.set_wall_velocity(uw)
+        lat.set_populations(f0)
+        lat.step(1)
+        got = lat.get_populations()
+    ref = O.step(f0, bc=bc, omega=om, mode=mode, uw=(uw, 0.0, 0.0))
+    assert rel(got, ref) <= 1e-12
+
+
 @pytest.mark.parametrize("nsteps", [2, 3, 10, 33, 70])
 @pytest.mark.parametrize("bc", [0, 1])
 def test_multi_step_fp64(nsteps, bc):
@@ -143,10 +166,11 @@ def test_tgv_32_fp64_200_steps_matches_oracle():
 
 @pytest.mark.parametrize("prec,unit", [("fp32", 0.0), ("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
 @pytest.mark.parametrize("bc", [0, 1])
-def test_one_step_reduced_precision(prec, unit, bc):
+@pytest.mark.parametrize("force", [True, False])  # without force: the unit-rate kernels
+def test_one_step_reduced_precision(prec, unit, bc, force):
     nx, ny, nz = 17, 9, 5
     f0 = near_eq_populations(nx, ny, nz, seed=11)
-    Fv = (1e-4, 0, 5e-5)
+    Fv = (1e-4, 0, 5e-5) if force else (0, 0, 0)
     om = O.rates(0.6)
     with make(nx, ny, nz, prec, bc, Fv, tau=0.6) as lat:
         lat.set_populations(f0)
