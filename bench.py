@@ -246,6 +246,24 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def kernel_name(F, workload, launch):
+    """The step kernel that ran, from the launch the autotuner chose (fpclbm_get_launch)."""
+    if workload == "shear2d":
+        return "fpc::k_step2d (D2Q9, AA even/odd)"
+    ens = workload == "ensemble"
+    v = launch["variant"]
+    if v == 2:
+        base = "fpc::k_ens_pair" if ens else "fpc::k_step_pair"
+        shape = "two cells per thread, blocks of 128"
+    elif v == 1:
+        base, shape = "fpc::k_step_pipe", "cp.async-pipelined, blocks of %d" % launch["block"]
+    else:
+        base = "fpc::k_ens_step" if ens else "fpc::k_step"
+        shape = "one cell per thread, blocks of %d" % launch["block"]
+    return "%s (AA even/odd; %s, register-cap class %d; collision mode %d: %s)" % (
+        base, shape, launch["minb"], launch["mode"], F.LAUNCH_MODES.get(launch["mode"], "?"))
+
+
 def time_ours(lat, F, torch, args, n, steps, warmup, inner):
     """Device-resident timing: CUDA events on the library's stream around `steps` fpclbm_step calls."""
     st = torch.cuda.current_stream()
@@ -338,7 +356,7 @@ def main():
         el = time_ours(lat, F, torch, args, ncell, args.steps, args.warmup, args.inner)
         ck = clocks.stop() if clocks else None
         el = max_over_ranks(el, world)
-        results[prec] = {"seconds": el, "clocks": ck}
+        results[prec] = {"seconds": el, "clocks": ck, "launch": lat.launch() if not two_d else None}
         if prec == prec0:
             # e2e: host buffers through the C ABI, copies inside the timed region
             nf = 3 if two_d else 4
@@ -372,9 +390,7 @@ def main():
     cfg.update({"precision": prec, "storage": prec, "lbm_steps_per_bench_step": args.inner,
                 "l2": "inputs larger than L2 (%.2f GB populations)" % (27 * BYTES[prec] * ncell / 1e9),
                 "parallelism": "replicas" if world > 1 else "1 GPU"})
-    kname = ("fpc::k_ens_step (persistent, AA even/odd)" if args.workload == "ensemble" else
-             "fpc::k_step2d (D2Q9, AA even/odd)" if two_d else
-             "fpc::k_step / fpc::k_step_pair (AA even/odd, the autotuner's variant)")
+    kname = kernel_name(F, args.workload, results[prec]["launch"])
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,

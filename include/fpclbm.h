@@ -20,6 +20,10 @@
  *   - Inputs are borrowed for the duration of the call.  Outputs are allocated
  *     by the caller.  "on_device" = 1 means the pointer is a CUDA device
  *     pointer on the handle's device; 0 means host memory (pinned or not).
+ *     Page-locked host memory that is mapped into the device's address space
+ *     (cudaHostAlloc, cudaHostRegister, pinned framework buffers) is read or
+ *     written in place by the field kernels over the host link; other host
+ *     memory goes through a device staging buffer.
  *   - The library owns every device allocation it makes; all device work is
  *     ordered on the stream given at creation (NULL = the legacy default
  *     stream).  Calls that return data synchronise that stream; fpclbm_step
@@ -216,6 +220,19 @@ FPCLBM_API int fpclbm_get_populations_at(fpclbm_t h, const long long* cells, int
 
 /* Steps taken since the last init_fields / set_populations. */
 FPCLBM_API int fpclbm_get_step_count(fpclbm_t h, long long* steps);
+
+/* Launch configuration of the step kernel, for reports (no counterpart in the
+ * paper: it names which of the library's equivalent kernels runs).  Valid after
+ * the first fpclbm_step since the last change of parameters, force or wall
+ * velocity (the autotuner chooses then); before that FPCLBM_ERR_STATE.
+ * out[0] threads per block; out[1] register-cap class (resident blocks of the
+ * one-cell kernel: 1 none, 2 ~128, 3 ~80, 4 64 registers); out[2] variant
+ * (0 one cell per thread, 1 cp.async-pipelined, 2 two cells per thread on the
+ * packed fp32 pipe; ensembles: 0 or 2); out[3] collision mode (0 FP, 1 MCM,
+ * 2 FP + learned closure, 3 FP + Smagorinsky, 4 FP and 5 MCM with every rate
+ * of orders 3-6 equal to 1 and no body force, where those moments are set to
+ * their attractors).  out is caller-owned int[4]. */
+FPCLBM_API int fpclbm_get_launch(fpclbm_t h, int out[4]);
 
 /* Install the learned closure used by FPCLBM_DIFF_FP_LEARNED: a per-cell
  * MLP 9 -> 64 -> 64 -> 1 (tanh hidden layers) whose inputs are the six

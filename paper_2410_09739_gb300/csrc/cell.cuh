@@ -205,4 +205,70 @@ __device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom&
     }
 }
 
+// Two neighbouring entries of one slot row (index c even, so the pair is 4- or
+// 8-byte aligned: every slot row starts 128-byte aligned) as one vector access.
+template <typename S>
+struct Store2;
+template <>
+struct Store2<float> {
+    __device__ __forceinline__ static f2 ld(const float* p) { return f2(*reinterpret_cast<const float2*>(p)); }
+    __device__ __forceinline__ static void st(float* p, f2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+};
+template <>
+struct Store2<__half> {
+    __device__ __forceinline__ static f2 ld(const __half* p)
+    {
+        return f2(__half22float2(*reinterpret_cast<const __half2*>(p)));
+    }
+    __device__ __forceinline__ static void st(__half* p, f2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
+};
+template <>
+struct Store2<__nv_bfloat16> {
+    __device__ __forceinline__ static f2 ld(const __nv_bfloat16* p)
+    {
+        return f2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)));
+    }
+    __device__ __forceinline__ static void st(__nv_bfloat16* p, f2 v)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
+    }
+};
+
+// Even step of the paired kernel with neighbouring cells c = 2t and c + 1 in
+// the two lanes: every access of the even step is to the cell's own slots, so
+// the two cells' values of a slot are adjacent and move as one vector load or
+// store (and, for 16-bit storage, one packed conversion).  A thread whose
+// second cell lies past the end (odd cell count) updates c alone.  Which
+// thread updates which cell is free within a step (each cell touches only its
+// own addresses), so the odd step keeps its own pairing.
+template <typename S, bool FORCE, int MODE>
+__device__ __forceinline__ void update_pair_even(S* __restrict__ buf, unsigned stride, unsigned t, unsigned ncells,
+                                                 const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5, f2 om6,
+                                                 f2 om8, f2 om9, int* flag)
+{
+    unsigned c = 2 * t;
+    const bool two = c + 1 < ncells;
+    f2 g[27];
+    if (two) {
+#pragma unroll
+        for (int s = 0; s < 27; ++s) g[s] = Store2<S>::ld(buf + (size_t)s * stride + c);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 27; ++s) {
+            const float v = Store<S>::ld(buf + (size_t)s * stride + c);
+            g[s] = f2(v, v);
+        }
+    }
+    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
+    if (!ok) atomicOr(flag, 1);
+    asm volatile("" : "+r"(c));  // rebuild the store addresses (see update_cell)
+    if (two) {
+#pragma unroll
+        for (int s = 0; s < 27; ++s) Store2<S>::st(buf + (size_t)(26 - s) * stride + c, g[s]);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 27; ++s) Store<S>::st(buf + (size_t)(26 - s) * stride + c, g[s].v.x);
+    }
+}
+
 }  // namespace fpc

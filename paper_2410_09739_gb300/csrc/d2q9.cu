@@ -27,6 +27,7 @@
 
 #include "collide.cuh"
 #include "fpclbm.h"
+#include "hostmem.h"
 #include "internal.h"
 
 namespace fpc {
@@ -476,11 +477,26 @@ int fpclbm2d_init_fields(fpclbm2d_t h, const double* rho, const double* ux, cons
     const size_t n = h->ncells;
     double* d = nullptr;
     const double *pr = rho, *px = ux, *py = uy;
+    if (!on_device) {  // page-locked host fields are read in place by the init kernel
+        const double *mr = mapped_host(rho), *mx = mapped_host(ux), *my = mapped_host(uy);
+        if (mr && mx && my) {
+            pr = mr;
+            px = mx;
+            py = my;
+            on_device = 1;
+        }
+    }
     if (!on_device) {
         FPC2_CK(h, cudaMalloc(&d, 3 * n * sizeof(double)), "staging");
-        cudaMemcpyAsync(d, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-        cudaMemcpyAsync(d + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-        cudaMemcpyAsync(d + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        cudaError_t ec = cudaMemcpyAsync(d, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (ec == cudaSuccess) ec = cudaMemcpyAsync(d + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (ec == cudaSuccess)
+            ec = cudaMemcpyAsync(d + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (ec != cudaSuccess) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(d);
+            FPC2_CK(h, ec, "copy fields");
+        }
         pr = d;
         px = d + n;
         py = d + 2 * n;
@@ -617,6 +633,13 @@ int fpclbm2d_moments(fpclbm2d_t h, double* rho, double* ux, double* uy, int on_d
     const size_t n = h->ncells;
     double* d = nullptr;
     double* o[3] = {rho, ux, uy};
+    if (!on_device) {  // page-locked host outputs are written in place by the moments kernel
+        double* m[3] = {mapped_host(rho), mapped_host(ux), mapped_host(uy)};
+        if ((!rho || m[0]) && (!ux || m[1]) && (!uy || m[2])) {
+            for (int k = 0; k < 3; ++k) o[k] = m[k];
+            on_device = 1;
+        }
+    }
     if (!on_device) {
         FPC2_CK(h, cudaMalloc(&d, 3 * n * sizeof(double)), "staging");
         for (int k = 0; k < 3; ++k) o[k] = o[k] ? d + k * n : nullptr;

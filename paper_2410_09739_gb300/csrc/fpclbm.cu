@@ -19,6 +19,7 @@
 
 #include "closure.cuh"
 #include "handle.h"
+#include "hostmem.h"
 
 using namespace fpc;
 
@@ -301,6 +302,7 @@ int ensure_stage(fpclbm* h, size_t bytes)
 }
 
 unsigned chunk_of(const Box& b) { return b.ncells < kChunk ? b.ncells : kChunk; }
+
 
 // ---------------------------------------------------------------------------
 // Autotuning of the launch configuration (block size; persistent grid for
@@ -606,6 +608,16 @@ int fpclbm_init_fields(fpclbm_t h, const double* rho, const double* ux, const do
     if (!h) return FPCLBM_ERR_ARG;
     h->err.clear();
     if (!rho || !ux || !uy || !uz) return fail(h, FPCLBM_ERR_ARG, "null field pointer");
+    if (!on_device) {  // page-locked host fields: the init kernel reads them in place
+        const double* m[4] = {mapped_host(rho), mapped_host(ux), mapped_host(uy), mapped_host(uz)};
+        if (m[0] && m[1] && m[2] && m[3]) {
+            rho = m[0];
+            ux = m[1];
+            uy = m[2];
+            uz = m[3];
+            on_device = 1;
+        }
+    }
     for (const Box& b : h->boxes) {
         const BoxGeom g = geom_of(h, b);
         if (on_device) {
@@ -783,6 +795,18 @@ int fpclbm_get_step_count(fpclbm_t h, long long* steps)
     return FPCLBM_OK;
 }
 
+int fpclbm_get_launch(fpclbm_t h, int out[4])
+{
+    if (!h || !out) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    if (!h->tuned) return fail(h, FPCLBM_ERR_STATE, "no launch chosen yet: the autotuner runs at the first step");
+    out[0] = h->block;
+    out[1] = h->minb;
+    out[2] = h->pipe;
+    out[3] = mode_of(h);
+    return FPCLBM_OK;
+}
+
 int fpclbm_moments(fpclbm_t h, double* rho, double* ux, double* uy, double* uz, int on_device)
 {
     if (!h) return FPCLBM_ERR_ARG;
@@ -790,6 +814,18 @@ int fpclbm_moments(fpclbm_t h, double* rho, double* ux, double* uy, double* uz, 
     if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
     const int parity = (int)(h->steps & 1);
     double* outs[4] = {rho, ux, uy, uz};
+    if (!on_device) {  // page-locked host outputs: the moments kernel writes them in place
+        bool all = true;
+        double* m[4];
+        for (int q = 0; q < 4; ++q) {
+            m[q] = mapped_host(outs[q]);
+            if (outs[q] && !m[q]) all = false;
+        }
+        if (all) {
+            for (int q = 0; q < 4; ++q) outs[q] = m[q];
+            on_device = 1;
+        }
+    }
     for (const Box& b : h->boxes) {
         const BoxGeom g = geom_of(h, b);
         if (on_device) {

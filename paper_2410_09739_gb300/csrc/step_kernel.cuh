@@ -138,10 +138,12 @@ cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
-// Paired variant: each thread updates cells c and c + half with the packed
-// fp32 arithmetic of pair.cuh (one instruction per operation for both cells).
-// Loads and stores stay per cell, so a warp's accesses are as coalesced as
-// in k_step; each cell still reads and writes only its own AA addresses.
+// Paired variant: each thread updates two cells with the packed fp32
+// arithmetic of pair.cuh (one instruction per operation for both cells).  The
+// odd step pairs cells c and c + half, with per-cell loads and stores as
+// coalesced as in k_step; the even step pairs neighbouring cells 2c, 2c + 1,
+// whose values of a slot are adjacent, with one vector access per slot.  Each
+// cell still reads and writes only its own AA addresses.
 // ---------------------------------------------------------------------------
 
 template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB>
@@ -157,7 +159,11 @@ __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, u
     G.div_nx = a.div_nx;
     G.div_nxny = a.div_nxny;
     const Rates<f2>& rt = a.rates;
-    update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, half, a.ncells, rt, a.Fx, a.Fy, a.Fz,
+    if (ODD)
+        update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, half, a.ncells, rt, a.Fx, a.Fy, a.Fz,
+                                             rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
+    else  // neighbouring cells 2 c1 and 2 c1 + 1, vector loads and stores
+        update_pair_even<S, FORCE, MODE>(static_cast<S*>(a.buf), a.stride, c1, a.ncells, rt, a.Fx, a.Fy, a.Fz,
                                          rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
 }
 
@@ -193,7 +199,10 @@ template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 cudaError_t step_go_pair(const StepArgs<float>& a, cudaStream_t st)
 {
     const unsigned half = (a.ncells + 1) / 2;
-    k_step_pair<S, ODD, BC, FORCE, MODE, 2 * MINB><<<(half + 127) / 128, 128, 0, st>>>(pair_args(a), half);
+    // the even step without force (vector accesses, no neighbour table, no source terms) fits in
+    // 96 registers without spilling: one block more per SM
+    constexpr int BLOCKS = (ODD || FORCE) ? 2 * MINB : 2 * MINB + 1;
+    k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS><<<(half + 127) / 128, 128, 0, st>>>(pair_args(a), half);
     return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ PRECISIONS = {"fp64": FPCLBM_FP64, "fp32": FPCLBM_FP32, "fp16": FPCLBM_FP32_STOR
 
 EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fpclbm_set_params",
             "fpclbm_set_rates", "fpclbm_set_force", "fpclbm_set_wall_velocity", "fpclbm_set_smagorinsky", "fpclbm_step", "fpclbm_moments", "fpclbm_diagnostics",
-            "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_set_closure",
+            "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_get_launch", "fpclbm_set_closure",
             "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc", "fpclbm_closure_sample",
             "fpclbm_closure_train", "fpclbm_closure_grad",
             "fpclbm2d_create", "fpclbm2d_init_fields", "fpclbm2d_set_params", "fpclbm2d_set_rates",
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
     L.fpclbm_get_populations_at.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, _P]
     L.fpclbm_set_populations.argtypes = [_P, _P]
     L.fpclbm_get_step_count.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong)]
+    L.fpclbm_get_launch.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
     L.fpclbm_set_closure.argtypes = [_P, ctypes.POINTER(ctypes.c_ushort), ctypes.c_int]
     L.fpclbm_diagnostics_noalloc.argtypes = [_P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, _P, _P]
@@ -231,6 +232,17 @@ def fpclbm_get_step_count(h) -> int:
     v = ctypes.c_longlong()
     _check(h, load().fpclbm_get_step_count(h, ctypes.byref(v)))
     return v.value
+
+
+LAUNCH_MODES = {0: "FP", 1: "MCM", 2: "FP + learned closure", 3: "FP + Smagorinsky",
+                4: "FP, unit rates of orders 3-6", 5: "MCM, unit rates of orders 3-6"}
+
+
+def fpclbm_get_launch(h) -> dict:
+    """The step kernel's launch: threads per block, register-cap class, variant, collision mode."""
+    v = (ctypes.c_int * 4)()
+    _check(h, load().fpclbm_get_launch(h, v))
+    return {"block": v[0], "minb": v[1], "variant": v[2], "mode": v[3]}
 
 
 def fpclbm_set_closure(h, bf16_bits):
@@ -389,6 +401,9 @@ class Lattice:
 
     def step_count(self) -> int:
         return fpclbm_get_step_count(self.h)
+
+    def launch(self) -> dict:
+        return fpclbm_get_launch(self.h)
 
     def set_closure(self, bf16_bits):
         return fpclbm_set_closure(self.h, bf16_bits)

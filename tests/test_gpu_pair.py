@@ -23,11 +23,15 @@ def near_eq(nx, ny, nz, seed, u_amp=0.05, noise=0.02):
     return f * (1.0 + noise * rng.uniform(-1, 1, f.shape))
 
 
-def run(monkeypatch, variant, shape, prec, bc, force, mode, f0, n):
+def run(monkeypatch, variant, shape, prec, bc, force, mode, f0, n, drift=None):
+    """drift None: 0.3 in the FP mode (general kernels), 0 in the MCM mode (without force: the
+    unit-rate kernels)."""
     monkeypatch.setenv("FPCLBM_LAUNCH", "128:2:%d" % variant)
     nx, ny, nz = shape
+    if drift is None:
+        drift = 0.3 if mode == 0 else 0.0
     with F.Lattice(nx, ny, nz, prec, bc) as lat:
-        lat.set_params(0.7, 0.3 if mode == 0 else 0.0, mode)
+        lat.set_params(0.7, drift, mode)
         lat.set_force(*((2e-4, -1e-4, 1e-4) if force else (0, 0, 0)))
         lat.set_populations(f0)
         fq = lat.get_populations()
@@ -64,3 +68,31 @@ def test_pair_equals_single_variant(monkeypatch, prec, shape):
     assert np.max(d) <= 40 * 1e-7 + 8 * ulp
     assert np.mean(d) <= 40 * 1e-8 + 0.25 * ulp
 
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 3, 3), (17, 9, 5), (33, 7, 6)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_pair_unit_rates_fp32_matches_oracle(monkeypatch, shape, bc):
+    """FP mode with the default rates and no force: the unit-rate paired kernels (the even step on
+    neighbouring cells with vector accesses, the odd step through the interior fast path)."""
+    nx, ny, nz = shape
+    f0 = near_eq(nx, ny, nz, 300 + nx + bc)
+    for n in (1, 2, 5):
+        fq, got = run(monkeypatch, 2, shape, "fp32", bc, False, 0, f0, n, drift=0.0)
+        ref = O.run(fq, n, bc=bc, omega=O.rates(0.7), mode=0)
+        assert np.max(np.abs(got - ref)) <= 1e-6 * n, n
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("shape", [(41, 33, 17), (64, 32, 31)])
+def test_pair_unit_rates_equals_single_variant(monkeypatch, prec, shape):
+    """40 steps of the unit-rate kernels, paired against one cell per thread (41 x 33 x 17 has an
+    odd cell count: the even step's last thread holds one cell)."""
+    nx, ny, nz = shape
+    f0 = near_eq(nx, ny, nz, 78)
+    _, a = run(monkeypatch, 0, shape, prec, 1, False, 0, f0, 40, drift=0.0)
+    _, b = run(monkeypatch, 2, shape, prec, 1, False, 0, f0, 40, drift=0.0)
+    ulp = {"fp32": 1e-6, "fp16": 2.0 ** -11 * 0.05, "bf16": 2.0 ** -8 * 0.05}[prec]
+    d = np.abs(a - b)
+    assert np.max(d) <= 40 * 1e-7 + 8 * ulp
+    assert np.mean(d) <= 40 * 1e-8 + 0.25 * ulp

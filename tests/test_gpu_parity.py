@@ -262,6 +262,69 @@ def test_parameter_and_state_errors():
             lat.set_force(float("nan"), 0, 0)
 
 
+def test_pinned_host_fields_equal_pageable():
+    """Page-locked host buffers are read and written in place by the kernels (no staging copy);
+    the results equal those of ordinary host memory bit for bit, for the 3D and the D2Q9 handle."""
+    torch = pytest.importorskip("torch")
+    nx, ny, nz = 19, 11, 7
+    flds = [np.ascontiguousarray(a).reshape(-1) for a in W.random_fields(nx, ny, nz, seed=12)]
+    pinned = [torch.from_numpy(a.copy()).pin_memory() for a in flds]
+    outs = {}
+    for kind, src in (("pageable", flds), ("pinned", [t.numpy() for t in pinned])):
+        with make(nx, ny, nz, "fp32", tau=0.7) as lat:
+            F.fpclbm_init_fields(lat.h, *src, on_device=0)
+            lat.step(3)
+            if kind == "pinned":
+                dst = [torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory() for _ in range(4)]
+                F.fpclbm_moments(lat.h, *[t.numpy() for t in dst], on_device=0)
+                outs[kind] = [t.numpy().copy() for t in dst]
+            else:
+                dst = [np.empty(nx * ny * nz) for _ in range(4)]
+                F.fpclbm_moments(lat.h, *dst, on_device=0)
+                outs[kind] = dst
+    for a, b in zip(outs["pageable"], outs["pinned"]):
+        assert np.array_equal(a, b)
+    L = 24
+    f2d = [np.ascontiguousarray(a).reshape(-1) for a in W.shear_layers(L, 0.05)]
+    p2d = [torch.from_numpy(a.copy()).pin_memory() for a in f2d]
+    res = []
+    for src, pin in ((f2d, False), ([t.numpy() for t in p2d], True)):
+        with F.Lattice2D(L, L, "fp32") as lat:
+            lat.set_params(0.6)
+            F.fpclbm2d_init_fields(lat.h, *src, on_device=0)
+            lat.step(3)
+            if pin:
+                dst = [torch.empty(L * L, dtype=torch.float64).pin_memory() for _ in range(3)]
+                F.fpclbm2d_moments(lat.h, *[t.numpy() for t in dst], on_device=0)
+                res.append([t.numpy().copy() for t in dst])
+            else:
+                dst = [np.empty(L * L) for _ in range(3)]
+                F.fpclbm2d_moments(lat.h, *dst, on_device=0)
+                res.append(dst)
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
+def test_launch_query_names_the_collision_mode():
+    with make(8, 8, 8, "fp32", tau=0.7) as lat:
+        lat.init_fields(*W.random_fields(8, 8, 8, seed=4))
+        with pytest.raises(F.FpclbmError):  # nothing chosen before the first step
+            lat.launch()
+        lat.step(2)
+        got = lat.launch()
+        assert got["mode"] == 4  # default rates, no force: FP with unit rates of orders 3-6
+        assert got["variant"] in (0, 1, 2) and got["block"] in (128, 256) and 1 <= got["minb"] <= 4
+        lat.set_force(1e-5, 0, 0)  # the general kernels
+        lat.step(2)
+        assert lat.launch()["mode"] == 0
+        lat.set_force(0, 0, 0)
+        om = O.rates(0.7)
+        om[12] = 1.1  # one third-order rate off 1: general kernels again
+        lat.set_rates(om)
+        lat.step(2)
+        assert lat.launch()["mode"] == 0
+
+
 def test_graph_replay_equals_single_launches_bitwise():
     n = 48
     rho, ux, uy, uz = W.tgv(n, 0.05)
