@@ -65,6 +65,9 @@
 #include <math.h>
 #include <stddef.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 27
 #define CS2 (1.0 / 3.0)
@@ -657,4 +660,23 @@ void orc_velocity_set(int* ex, int* ey, int* ez)
 void orc_moment_exponents(int* mnp)
 {
     for (int i = 0; i < Q; ++i) { mnp[3 * i] = MNP[i][0]; mnp[3 * i + 1] = MNP[i][1]; mnp[3 * i + 2] = MNP[i][2]; }
+}
+
+/* Timing of the oracle as a CPU baseline: threads of the parallel loops (n >= 1; no effect
+ * without OpenMP), and the count the runtime will use. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

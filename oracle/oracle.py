@@ -19,7 +19,7 @@ from . import build as _build
 __all__ = [
     "lib", "velocity_set", "moment_exponents", "central_matrix", "grouping_matrix",
     "attractor_generic", "maxwell_moments", "collide", "equilibrium", "init_equilibrium",
-    "step", "run", "moments", "rates", "threads", "EQ_MODE_FP", "EQ_MODE_MCM",
+    "step", "run", "moments", "rates", "threads", "set_threads", "EQ_MODE_FP", "EQ_MODE_MCM",
     "BC_PERIODIC", "BC_WALLS_Y", "BC_BOX", "BC_HALF_CHANNEL", "smagorinsky_tau",
 ]
 
@@ -206,6 +206,12 @@ def rates(tau: float, drift: float = 0.0) -> np.ndarray:
 
 
 def threads() -> int:
-    """Threads the OpenMP runtime will use (OMP_NUM_THREADS or all cores)."""
-    v = os.environ.get("OMP_NUM_THREADS")
-    return int(v) if v else (os.cpu_count() or 1)
+    """Threads the OpenMP runtime will use for the oracle's parallel loops."""
+    L = lib()
+    L.orc_max_threads.restype = ctypes.c_int
+    return int(L.orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (CPU-baseline timing)."""
+    lib().orc_set_threads(ctypes.c_int(int(n)))

@@ -68,6 +68,46 @@ __device__ __forceinline__ void inv3(R& k0, R& k1, R& k2, R u, R u2, R tu, R K)
     k2 = hi;
 }
 
+// inv3 for a line some of whose inputs are known to be zero (Z0, Z1, Z2 for
+// k0, k1, k2): the terms they would feed are left out.  Used in the unit-rate
+// modes, where the moments of orders 3 and 5 are exactly zero after the
+// collision.  A line with K0 && Z0 && Z1 && Z2 does not occur.
+template <typename R, bool K0, bool Z0, bool Z1, bool Z2>
+__device__ __forceinline__ void inv3z(R& k0, R& k1, R& k2, R u, R u2, R tu, R K)
+{
+    constexpr bool UZ = K0 && Z0;  // U = K + k0 vanishes
+    R U = R(0);
+    if constexpr (!UZ) {
+        if constexpr (K0) U = k0;
+        else if constexpr (Z0) U = K;
+        else U = K + k0;
+    }
+    R M1;
+    if constexpr (UZ) M1 = k1;
+    else if constexpr (Z1) M1 = u * U;
+    else M1 = fmaR(u, U, k1);
+    R M2;
+    if constexpr (Z1 && Z2) {
+        M2 = u2 * U;
+    } else {
+        R t;
+        if constexpr (Z1) t = k2;
+        else if constexpr (Z2) t = tu * k1;
+        else t = fmaR(tu, k1, k2);
+        if constexpr (UZ) M2 = t;
+        else M2 = fmaR(u2, U, t);
+    }
+    const R h = R(0.5) * M1;
+    const R lo = fmaR(R(0.5), M2, -h);
+    const R hi = fmaR(R(0.5), M2, h);
+    R mid;
+    if constexpr (Z0) mid = -M2;
+    else mid = k0 - M2;
+    k0 = lo;
+    k1 = mid;
+    k2 = hi;
+}
+
 // Rest constants of the three passes (axis z first, then y, then x).
 // Pass A (z lines at fixed (ix, iy)): K = w1(ix) w1(iy)
 // Pass B (y lines at fixed (ix, p)):  K = w1(ix) r1(p)
@@ -401,7 +441,24 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     }
 
     // ---- Steps 4+5: back to populations (passes in reverse order) ----
-    FPC_PASS_C(inv3)
+    if constexpr (R1) {
+        // x lines at fixed (n, p); inputs of total order 3 or 5 are zero
+#define FPC_INVC(n, p, Z0, Z1, Z2)                                                                        \
+    inv3z<R, r1(n) * r1(p) == 0.0, Z0, Z1, Z2>(g[3 * (n) + 9 * (p)], g[1 + 3 * (n) + 9 * (p)],           \
+                                               g[2 + 3 * (n) + 9 * (p)], ux, ux2, tux, R(r1(n) * r1(p)))
+        FPC_INVC(0, 0, false, false, false);
+        FPC_INVC(1, 0, false, false, true);
+        FPC_INVC(2, 0, false, true, false);
+        FPC_INVC(0, 1, false, false, true);
+        FPC_INVC(1, 1, false, true, false);
+        FPC_INVC(2, 1, true, false, true);
+        FPC_INVC(0, 2, false, true, false);
+        FPC_INVC(1, 2, true, false, true);
+        FPC_INVC(2, 2, false, true, false);
+#undef FPC_INVC
+    } else {
+        FPC_PASS_C(inv3)
+    }
     FPC_PASS_B(inv3)
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
