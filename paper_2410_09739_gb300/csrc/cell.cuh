@@ -271,4 +271,61 @@ __device__ __forceinline__ void update_pair_even(S* __restrict__ buf, unsigned s
     }
 }
 
+// Odd step of the paired kernel for boxes with nx even: neighbouring cells
+// c = 2t (x even) and c + 1 share y and z, hence the neighbour table.  For the
+// nine slots with e_x = 0 their two values (neighbour reads, bounce-back
+// redirects to their own slots, and writes) sit side by side, 2-element
+// aligned: one vector access per slot.  For the other eighteen slots the
+// second cell's address is the first one's plus 1, minus nx where the
+// second cell's neighbour column wraps (x + 2 = nx for a neighbour at x + 1
+// of the first cell, x = 0 for one at x - 1); a bounce-back redirect stays
+// within the cells' own slots (plus 1).  Periodic x only (no closed box).
+template <typename S, int BC, bool FORCE, int MODE>
+__device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const CellGeom& G, unsigned t,
+                                                    const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5,
+                                                    f2 om6, f2 om8, f2 om9, int* flag)
+{
+    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y, "periodic x, resting walls");
+    const unsigned stride = G.stride;
+    unsigned c = 2 * t;
+    f2 g[27];
+    {
+        const Nbr n = make_nbr<BC>(G, c);
+        const int x = (int)n.xs[1];
+        const int wp = x + 2 == G.nx ? -G.nx : 0;  // second cell's column x + 2 wraps
+        const int wm = x == 0 ? -G.nx : 0;         // first cell's column x - 1 wrapped
+#pragma unroll
+        for (int s = 0; s < 27; ++s) {
+            const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
+            S* p = load_ptr<S, true, BC>(buf, s, n, stride, c);
+            if (ix == 1) {
+                g[s] = Store2<S>::ld(p);
+            } else {  // the read is at x - e_x: x + 1 for ix = 0, x - 1 for ix = 2
+                const int w = inside<BC>(n, ix, iy, iz) ? (ix == 0 ? wp : wm) : 0;
+                g[s].v.x = Store<S>::ld(p);
+                g[s].v.y = Store<S>::ld(p + 1 + w);
+            }
+        }
+    }
+    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
+    if (!ok) atomicOr(flag, 1);
+    asm volatile("" : "+r"(c));  // rebuild the store addresses (see update_cell)
+    const Nbr n = make_nbr<BC>(G, c);
+    const int x = (int)n.xs[1];
+    const int wp = x + 2 == G.nx ? -G.nx : 0;
+    const int wm = x == 0 ? -G.nx : 0;
+#pragma unroll
+    for (int s = 0; s < 27; ++s) {
+        const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
+        S* p = store_ptr<S, true, BC>(buf, s, n, stride, c);
+        if (ix == 1) {
+            Store2<S>::st(p, g[s]);
+        } else {  // the write is at x + e_x: x + 1 for ix = 2, x - 1 for ix = 0
+            const int w = inside<BC>(n, 2 - ix, 2 - iy, 2 - iz) ? (ix == 2 ? wp : wm) : 0;
+            Store<S>::st(p, g[s].v.x);
+            Store<S>::st(p + 1 + w, g[s].v.y);
+        }
+    }
+}
+
 }  // namespace fpc

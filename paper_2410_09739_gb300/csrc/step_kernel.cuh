@@ -146,7 +146,7 @@ cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
 // cell still reads and writes only its own AA addresses.
 // ---------------------------------------------------------------------------
 
-template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB>
+template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB, bool ADJ>
 __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, unsigned half)
 {
     const unsigned c1 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -159,7 +159,10 @@ __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, u
     G.div_nx = a.div_nx;
     G.div_nxny = a.div_nxny;
     const Rates<f2>& rt = a.rates;
-    if (ODD)
+    if (ODD && ADJ)  // nx even: neighbouring cells 2 c1, 2 c1 + 1 with a shared neighbour table
+        update_pair_odd_adj<S, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, rt, a.Fx, a.Fy, a.Fz, rt.om[4],
+                                                rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
+    else if (ODD)  // odd nx: cells c1 and c1 + half
         update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, half, a.ncells, rt, a.Fx, a.Fy, a.Fz,
                                              rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
     else  // neighbouring cells 2 c1 and 2 c1 + 1, vector loads and stores
@@ -202,7 +205,11 @@ cudaError_t step_go_pair(const StepArgs<float>& a, cudaStream_t st)
     // the even step without force (vector accesses, no neighbour table, no source terms) fits in
     // 96 registers without spilling: one block more per SM
     constexpr int BLOCKS = (ODD || FORCE) ? 2 * MINB : 2 * MINB + 1;
-    k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS><<<(half + 127) / 128, 128, 0, st>>>(pair_args(a), half);
+    const unsigned grid = (half + 127) / 128;
+    if (ODD && (a.nx & 1) == 0)
+        k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS, true><<<grid, 128, 0, st>>>(pair_args(a), half);
+    else
+        k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS, false><<<grid, 128, 0, st>>>(pair_args(a), half);
     return cudaGetLastError();
 }
 
