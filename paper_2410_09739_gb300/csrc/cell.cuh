@@ -133,6 +133,29 @@ __device__ __forceinline__ void lid_correct(R g[27], R lid6x, R lid6z)
     }
 }
 
+// Whether a cell lies in the top row y = ny - 1 (the moving wall's neighbours).
+__device__ __forceinline__ bool top_row(const CellGeom& G, unsigned cell)
+{
+    const unsigned y = fdiv(cell - fdiv(cell, G.div_nxny) * (unsigned)(G.nx * G.ny), G.div_nx);
+    return y + 1 == (unsigned)G.ny;
+}
+
+// The moving-wall correction for the lanes of a pair whose cell lies in the
+// top row: the other lane's wall velocity is masked to zero, which leaves its
+// values unchanged (g - 0 = g).
+template <int BC>
+__device__ __forceinline__ void lid_correct_pair(f2 (&g)[27], const CellGeom& G, unsigned ca, unsigned cb, f2 lid6x,
+                                                 f2 lid6z)
+{
+    if constexpr (BC == BC_WALLS_Y_LID || BC == BC_BOX_LID) {
+        const bool ta = top_row(G, ca), tb = top_row(G, cb);
+        if (ta || tb) {
+            const f2 m(ta ? 1.f : 0.f, tb ? 1.f : 0.f);
+            lid_correct(g, lid6x * m, lid6z * m);
+        }
+    }
+}
+
 // active = false: the lane only takes part in warp-collective work (learned
 // mode); it reads a valid cell but writes nothing.
 template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE>
@@ -171,13 +194,14 @@ __device__ __forceinline__ void update_cell(S* __restrict__ buf, const CellGeom&
 // when it is below ncells) are loaded into the lanes of f2 values, collided
 // with packed fp32 arithmetic and stored back, each cell at its own AA
 // addresses.  c2 is recomputed after the collision (from the uniform half)
-// rather than kept live through it.  Resting walls only.
+// rather than kept live through it.  Every boundary kind; the moving-wall
+// correction is applied per lane.
 template <typename S, bool ODD, int BC, bool FORCE, int MODE>
 __device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom& G, unsigned c1, unsigned half,
                                             unsigned ncells, const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4,
-                                            f2 om5, f2 om6, f2 om8, f2 om9, int* flag)
+                                            f2 om5, f2 om6, f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0),
+                                            f2 lid6z = f2(0.0))
 {
-    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_HALF_CHANNEL, "resting walls only");
     const unsigned stride = G.stride;
     f2 g[27];
     {
@@ -193,6 +217,7 @@ __device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom&
     const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
     if (!ok) atomicOr(flag, 1);
     asm volatile("" : "+r"(c1));  // rebuild the store addresses (see update_cell)
+    lid_correct_pair<BC>(g, G, c1, c1 + half < ncells ? c1 + half : c1, lid6x, lid6z);
     Nbr n;
     if (ODD) n = make_nbr<BC>(G, c1);
 #pragma unroll
@@ -241,11 +266,12 @@ struct Store2<__nv_bfloat16> {
 // second cell lies past the end (odd cell count) updates c alone.  Which
 // thread updates which cell is free within a step (each cell touches only its
 // own addresses), so the odd step keeps its own pairing.
-template <typename S, bool FORCE, int MODE>
-__device__ __forceinline__ void update_pair_even(S* __restrict__ buf, unsigned stride, unsigned t, unsigned ncells,
+template <typename S, int BC, bool FORCE, int MODE>
+__device__ __forceinline__ void update_pair_even(S* __restrict__ buf, const CellGeom& G, unsigned t, unsigned ncells,
                                                  const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5, f2 om6,
-                                                 f2 om8, f2 om9, int* flag)
+                                                 f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0), f2 lid6z = f2(0.0))
 {
+    const unsigned stride = G.stride;
     unsigned c = 2 * t;
     const bool two = c + 1 < ncells;
     f2 g[27];
@@ -262,6 +288,7 @@ __device__ __forceinline__ void update_pair_even(S* __restrict__ buf, unsigned s
     const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
     if (!ok) atomicOr(flag, 1);
     asm volatile("" : "+r"(c));  // rebuild the store addresses (see update_cell)
+    lid_correct_pair<BC>(g, G, c, two ? c + 1 : c, lid6x, lid6z);
     if (two) {
 #pragma unroll
         for (int s = 0; s < 27; ++s) Store2<S>::st(buf + (size_t)(26 - s) * stride + c, g[s]);
@@ -283,9 +310,10 @@ __device__ __forceinline__ void update_pair_even(S* __restrict__ buf, unsigned s
 template <typename S, int BC, bool FORCE, int MODE>
 __device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const CellGeom& G, unsigned t,
                                                     const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5,
-                                                    f2 om6, f2 om8, f2 om9, int* flag)
+                                                    f2 om6, f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0),
+                                                    f2 lid6z = f2(0.0))
 {
-    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y, "periodic x, resting walls");
+    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_WALLS_Y_LID, "periodic x, walls in y only");
     const unsigned stride = G.stride;
     unsigned c = 2 * t;
     f2 g[27];
@@ -310,6 +338,7 @@ __device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const C
     const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
     if (!ok) atomicOr(flag, 1);
     asm volatile("" : "+r"(c));  // rebuild the store addresses (see update_cell)
+    lid_correct_pair<BC>(g, G, c, c + 1, lid6x, lid6z);
     const Nbr n = make_nbr<BC>(G, c);
     const int x = (int)n.xs[1];
     const int wp = x + 2 == G.nx ? -G.nx : 0;

@@ -46,9 +46,10 @@ __global__ void __launch_bounds__(256, MINB) k_ens_step(const EnsArgs a)
     }
 }
 
-// Paired variant (pair.cuh): on the odd step a tile's cells t and t + tile/2
-// share a thread; on the even step neighbouring cells 2t, 2t + 1 do, with one
-// vector access per slot (see update_pair_even).
+// Paired variant (pair.cuh): neighbouring cells 2t, 2t + 1 of a tile share a
+// thread (one vector access per slot where the pair's values are adjacent; see
+// update_pair_even and update_pair_odd_adj), except on the odd step of a box
+// with odd nx, where cells t and t + tile/2 do.
 template <bool ODD, bool FORCE, int MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_ens_pair(const EnsArgs a)
 {
@@ -74,15 +75,19 @@ __global__ void __launch_bounds__(128, MINB) k_ens_pair(const EnsArgs a)
         const f2 om2(om, om);
         float* buf = base + __ldg(&B.off);
         for (unsigned c = threadIdx.x; c < half; c += blockDim.x) {
-            if (ODD) {
+            if (ODD && (G.nx & 1) == 0) {  // even nx: neighbouring cells, shared neighbour table
+                if (first + 2 * c >= ncells) break;
+                update_pair_odd_adj<float, BC_PERIODIC, FORCE, MODE>(buf, G, first / 2 + c, a.rates2, a.Fx2, a.Fy2,
+                                                                     a.Fz2, om2, om2, om2, om2, om2, a.flag);
+            } else if (ODD) {
                 const unsigned c1 = first + c;
                 if (c1 >= ncells) break;
                 update_pair<float, ODD, BC_PERIODIC, FORCE, MODE>(buf, G, c1, half, ncells, a.rates2, a.Fx2, a.Fy2,
                                                                   a.Fz2, om2, om2, om2, om2, om2, a.flag);
             } else {  // neighbouring cells first + 2c, first + 2c + 1 (tiles and box blocks are even-aligned)
                 if (first + 2 * c >= ncells) break;
-                update_pair_even<float, FORCE, MODE>(buf, G.stride, first / 2 + c, ncells, a.rates2, a.Fx2, a.Fy2,
-                                                     a.Fz2, om2, om2, om2, om2, om2, a.flag);
+                update_pair_even<float, BC_PERIODIC, FORCE, MODE>(buf, G, first / 2 + c, ncells, a.rates2, a.Fx2,
+                                                                  a.Fy2, a.Fz2, om2, om2, om2, om2, om2, a.flag);
             }
         }
     }

@@ -389,8 +389,8 @@ int autotune(fpclbm* h)
     const bool fp32_math = h->precision != FPCLBM_FP64 && plain_mode(md);
     const bool pipe_ok = elem_size(h->precision) >= 4 && plain_mode(md) &&
                          (kb == BC_PERIODIC || kb == BC_WALLS_Y);
-    // paired variant (two cells per thread, packed fp32): fp32 arithmetic, periodic and channel
-    const bool pair_ok = fp32_math && (kb == BC_PERIODIC || kb == BC_WALLS_Y);
+    // paired variant (two cells per thread, packed fp32): fp32 arithmetic, every boundary kind
+    const bool pair_ok = fp32_math;
     if (h->ensemble) {
         for (int minb : {2, 3})
             for (int block : {128, 256}) {

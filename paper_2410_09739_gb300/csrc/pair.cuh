@@ -29,6 +29,7 @@ __device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, 
 __device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
 __device__ __forceinline__ f2 operator-(f2 a) { return f2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
 __device__ __forceinline__ f2& operator+=(f2& a, f2 b) { return a = a + b; }
+__device__ __forceinline__ f2& operator-=(f2& a, f2 b) { return a = a - b; }
 __device__ __forceinline__ f2 operator/(f2 a, f2 b) { return f2(make_float2(a.v.x / b.v.x, a.v.y / b.v.y)); }
 __device__ __forceinline__ bool operator>(f2 a, f2 b) { return a.v.x > b.v.x && a.v.y > b.v.y; }
 __device__ __forceinline__ bool operator<(f2 a, f2 b) { return a.v.x < b.v.x && a.v.y < b.v.y; }

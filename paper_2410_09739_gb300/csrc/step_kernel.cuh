@@ -159,15 +159,17 @@ __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, u
     G.div_nx = a.div_nx;
     G.div_nxny = a.div_nxny;
     const Rates<f2>& rt = a.rates;
-    if (ODD && ADJ)  // nx even: neighbouring cells 2 c1, 2 c1 + 1 with a shared neighbour table
+    if constexpr (ODD && ADJ)  // neighbouring cells 2 c1, 2 c1 + 1 with a shared neighbour table
         update_pair_odd_adj<S, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, rt, a.Fx, a.Fy, a.Fz, rt.om[4],
-                                                rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
-    else if (ODD)  // odd nx: cells c1 and c1 + half
+                                                rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag, a.lid6x, a.lid6z);
+    else if constexpr (ODD)  // cells c1 and c1 + half
         update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, half, a.ncells, rt, a.Fx, a.Fy, a.Fz,
-                                             rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
+                                             rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag, a.lid6x,
+                                             a.lid6z);
     else  // neighbouring cells 2 c1 and 2 c1 + 1, vector loads and stores
-        update_pair_even<S, FORCE, MODE>(static_cast<S*>(a.buf), a.stride, c1, a.ncells, rt, a.Fx, a.Fy, a.Fz,
-                                         rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag);
+        update_pair_even<S, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, a.ncells, rt, a.Fx, a.Fy, a.Fz,
+                                             rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag, a.lid6x,
+                                             a.lid6z);
 }
 
 // The launch arguments with every scalar duplicated into both lanes.
@@ -202,12 +204,15 @@ template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 cudaError_t step_go_pair(const StepArgs<float>& a, cudaStream_t st)
 {
     const unsigned half = (a.ncells + 1) / 2;
-    // the even step without force (vector accesses, no neighbour table, no source terms) fits in
-    // 96 registers without spilling: one block more per SM
-    constexpr int BLOCKS = (ODD || FORCE) ? 2 * MINB : 2 * MINB + 1;
+    // the even step without force or moving wall (vector accesses, no neighbour table, no source
+    // terms) fits in 96 registers without spilling: one block more per SM
+    constexpr bool LID = BC == BC_WALLS_Y_LID || BC == BC_BOX_LID;
+    constexpr int BLOCKS = (ODD || FORCE || LID) ? 2 * MINB : 2 * MINB + 1;
     const unsigned grid = (half + 127) / 128;
-    if (ODD && (a.nx & 1) == 0)
-        k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS, true><<<grid, 128, 0, st>>>(pair_args(a), half);
+    // neighbouring cells on the odd step: x periodic and nx even (rows hold whole pairs)
+    constexpr bool ADJ_OK = ODD && (BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_WALLS_Y_LID);
+    if (ADJ_OK && (a.nx & 1) == 0)
+        k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS, ADJ_OK><<<grid, 128, 0, st>>>(pair_args(a), half);
     else
         k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS, false><<<grid, 128, 0, st>>>(pair_args(a), half);
     return cudaGetLastError();
@@ -216,9 +221,9 @@ cudaError_t step_go_pair(const StepArgs<float>& a, cudaStream_t st)
 template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE, int MINB>
 cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
-    // paired variant: fp32 arithmetic, FP and MCM modes, periodic and channel boxes, one register
-    // cap (4 blocks of 128 threads: 128 registers hold two cells without spilling)
-    if constexpr (sizeof(R) == 4 && plain_mode(MODE) && BC <= BC_WALLS_Y && MINB == 2) {
+    // paired variant: fp32 arithmetic, FP and MCM modes, every boundary kind, one register cap
+    // (4 blocks of 128 threads: 128 registers hold two cells without spilling)
+    if constexpr (sizeof(R) == 4 && plain_mode(MODE) && MINB == 2) {
         if (cfg.pipe == 2) return step_go_pair<S, ODD, BC, FORCE, MODE, MINB>(a, st);
     }
     // the pipelined variant retires tail lanes early, so it never runs the warp-collective

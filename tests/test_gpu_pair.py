@@ -96,3 +96,26 @@ def test_pair_unit_rates_equals_single_variant(monkeypatch, prec, shape):
     d = np.abs(a - b)
     assert np.max(d) <= 40 * 1e-7 + 8 * ulp
     assert np.mean(d) <= 40 * 1e-8 + 0.25 * ulp
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 4), (7, 6, 5), (16, 9, 6)])
+@pytest.mark.parametrize("bc,lid", [(1, 0.05), (2, 0.05), (2, 0.0), (3, 0.0)])
+@pytest.mark.parametrize("drift", [0.0, 0.3])
+def test_pair_walls_and_lid_match_oracle(monkeypatch, shape, bc, lid, drift):
+    """The paired kernel on a channel with a moving top wall, the closed box (lid moving or at rest)
+    and the half channel, against the oracle: the moving-wall correction is applied per lane, and
+    even nx takes the neighbouring-cell odd step where x is periodic (channel)."""
+    monkeypatch.setenv("FPCLBM_LAUNCH", "128:2:2")
+    nx, ny, nz = shape
+    f0 = near_eq(nx, ny, nz, 900 + nx + 10 * bc + int(100 * lid))
+    with F.Lattice(nx, ny, nz, "fp32", bc) as lat:
+        lat.set_params(0.7, drift)
+        if lid:
+            lat.set_wall_velocity(lid)
+        lat.set_populations(f0)
+        fq = lat.get_populations()
+        lat.step(5)
+        got = lat.get_populations()
+        assert lat.launch()["variant"] == 2
+    ref = O.run(fq, 5, bc=bc, omega=O.rates(0.7, drift), uw=(lid, 0.0, 0.0))
+    assert np.max(np.abs(got - ref)) <= 5e-6
