@@ -99,7 +99,8 @@ def peaks():
 
 
 STEP_KERNEL_SOURCES = ("common.cuh", "collide.cuh", "pair.cuh", "closure.cuh", "cell.cuh", "step_kernel.cuh", "step_fp32.cu",
-                       "step_fp16.cu", "step_bf16.cu", "step_fp64.cu", "step_kernels.cu", "internal.h")
+                       "step_fp32_odd.cu", "step_fp16.cu", "step_fp16_odd.cu", "step_bf16.cu", "step_bf16_odd.cu",
+                       "step_fp64.cu", "step_kernels.cu", "internal.h")
 
 
 def kernel_source_hash():

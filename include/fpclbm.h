@@ -230,8 +230,8 @@ FPCLBM_API int fpclbm_get_step_count(fpclbm_t h, long long* steps);
  * (0 one cell per thread, 1 cp.async-pipelined, 2 two cells per thread on the
  * packed fp32 pipe; ensembles: 0 or 2); out[3] collision mode (0 FP, 1 MCM,
  * 2 FP + learned closure, 3 FP + Smagorinsky, 4 FP and 5 MCM with every rate
- * of orders 3-6 equal to 1 and no body force, where those moments are set to
- * their attractors).  out is caller-owned int[4]. */
+ * of orders 3-6 equal to 1, where those moments are set to their attractors
+ * plus half their body-force sources).  out is caller-owned int[4]. */
 FPCLBM_API int fpclbm_get_launch(fpclbm_t h, int out[4]);
 
 /* Install the learned closure used by FPCLBM_DIFF_FP_LEARNED: a per-cell

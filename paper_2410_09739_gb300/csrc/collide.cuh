@@ -25,11 +25,12 @@
 // Readings: first-order moments enter attractors and sources as 0; sources
 // use pre-collision moments; attractors of orders 4-6 use post-collision
 // lower moments; kappa^Mv_122 carries Pi_110 Pi_012 (continuous form).
-// In the modes *_R1 (rates of orders 3-6 equal to 1, no force) the moments of
-// orders 3-6 are set to their attractors; the third- and fifth-order
-// attractors vanish there (they are built from odd moments that are zero
-// after the collision), and the unused pre-collision moments of those orders
-// drop out of the forward transform.
+// In the modes *_R1 (rates of orders 3-6 equal to 1) the moments of orders 3-6
+// are set to their attractors plus half their sources, kappa~ = kappa^Mv +
+// sigma / 2, with no grouping.  Without force the third- and fifth-order
+// moments then vanish (attractors built from odd moments that are zero after
+// the collision), and the unused pre-collision moments of orders 3-6 drop out
+// of the forward transform.
 #pragma once
 #include "common.cuh"
 #include "pair.cuh"
@@ -153,7 +154,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
                                              R om8, R om9, const float* closure, R c2 = R(0))
 {
     constexpr bool R1 = r1_mode(MODE);
-    static_assert(!(R1 && FORCE), "the unit-rate modes carry no body force");
+    constexpr bool ODD0 = R1 && !FORCE;  // moments of orders 3 and 5 exactly zero after the collision
     // ---- Step 7 and the first pass (z lines), sharing the line sums ----
     R S[9], Dz[9], Pz[9];
 #pragma unroll
@@ -298,10 +299,18 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     }
 
     // order 3 (attractors 0): pairs (120,102), (210,012), (201,021), and 111
-    if constexpr (R1) {
+    if constexpr (ODD0) {
         FPC_D(1, 2, 0) = FPC_D(1, 0, 2) = FPC_D(2, 1, 0) = R(0);
         FPC_D(0, 1, 2) = FPC_D(2, 0, 1) = FPC_D(0, 2, 1) = R(0);
         FPC_D(1, 1, 1) = R(0);
+    } else if constexpr (R1) {  // with force: half the sources
+        FPC_D(1, 2, 0) = R(0.5) * s120;
+        FPC_D(1, 0, 2) = R(0.5) * s102;
+        FPC_D(2, 1, 0) = R(0.5) * s210;
+        FPC_D(0, 1, 2) = R(0.5) * s012;
+        FPC_D(2, 0, 1) = R(0.5) * s201;
+        FPC_D(0, 2, 1) = R(0.5) * s021;
+        FPC_D(1, 1, 1) = R(0.5) * s111;
     } else {
 #define FPC_PAIR3(A, B, sa, sb, j)                                                      \
     {                                                                                   \
@@ -351,12 +360,21 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
             A112 = fmaR(third + pc, o110, R(2) * o011 * o101) * inv_rho;
         }
         if constexpr (R1) {
-            FPC_D(2, 2, 0) = A220;
-            FPC_D(2, 0, 2) = A202;
-            FPC_D(0, 2, 2) = A022;
-            FPC_D(2, 1, 1) = A211;
-            FPC_D(1, 2, 1) = A121;
-            FPC_D(1, 1, 2) = A112;
+            if constexpr (FORCE) {
+                FPC_D(2, 2, 0) = fmaR(R(0.5), s220, A220);
+                FPC_D(2, 0, 2) = fmaR(R(0.5), s202, A202);
+                FPC_D(0, 2, 2) = fmaR(R(0.5), s022, A022);
+                FPC_D(2, 1, 1) = fmaR(R(0.5), s211, A211);
+                FPC_D(1, 2, 1) = fmaR(R(0.5), s121, A121);
+                FPC_D(1, 1, 2) = fmaR(R(0.5), s112, A112);
+            } else {
+                FPC_D(2, 2, 0) = A220;
+                FPC_D(2, 0, 2) = A202;
+                FPC_D(0, 2, 2) = A022;
+                FPC_D(2, 1, 1) = A211;
+                FPC_D(1, 2, 1) = A121;
+                FPC_D(1, 1, 2) = A112;
+            }
         } else {
         const R d220 = FPC_D(2, 2, 0), d202 = FPC_D(2, 0, 2), d022 = FPC_D(0, 2, 2);
         const R y4s = (d220 + d202) + d022, y4d1 = (d220 + d202) - d022, y4d2 = d220 - d202;
@@ -391,7 +409,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     if (FORCE) s222 = R(2) * ((fx * FPC_D(1, 2, 2) + fy * FPC_D(2, 1, 2)) + fz * FPC_D(2, 2, 1));
 
     // order 5: attractors from post-collision second and third moments
-    if constexpr (R1) {
+    if constexpr (ODD0) {
         FPC_D(1, 2, 2) = FPC_D(2, 1, 2) = FPC_D(2, 2, 1) = R(0);
     } else {
         R A122 = R(0), A212 = R(0), A221 = R(0);
@@ -406,17 +424,23 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
             A221 = c * (fmaR(K200, FPC_D(0, 2, 1), K020 * FPC_D(2, 0, 1)) +
                         fmaR(R(4) * o110, k111, R(2) * fmaR(o011, FPC_D(2, 1, 0), o101 * FPC_D(1, 2, 0))));
         }
-        R t122 = fmaR(rt.om[23], A122, rt.keep[23] * FPC_D(1, 2, 2));
-        R t212 = fmaR(rt.om[24], A212, rt.keep[24] * FPC_D(2, 1, 2));
-        R t221 = fmaR(rt.om[25], A221, rt.keep[25] * FPC_D(2, 2, 1));
-        if (FORCE) {
-            t122 = fmaR(rt.src[23], s122, t122);
-            t212 = fmaR(rt.src[24], s212, t212);
-            t221 = fmaR(rt.src[25], s221, t221);
+        if constexpr (R1) {  // with force (ODD0 handled above)
+            FPC_D(1, 2, 2) = fmaR(R(0.5), s122, A122);
+            FPC_D(2, 1, 2) = fmaR(R(0.5), s212, A212);
+            FPC_D(2, 2, 1) = fmaR(R(0.5), s221, A221);
+        } else {
+            R t122 = fmaR(rt.om[23], A122, rt.keep[23] * FPC_D(1, 2, 2));
+            R t212 = fmaR(rt.om[24], A212, rt.keep[24] * FPC_D(2, 1, 2));
+            R t221 = fmaR(rt.om[25], A221, rt.keep[25] * FPC_D(2, 2, 1));
+            if (FORCE) {
+                t122 = fmaR(rt.src[23], s122, t122);
+                t212 = fmaR(rt.src[24], s212, t212);
+                t221 = fmaR(rt.src[25], s221, t221);
+            }
+            FPC_D(1, 2, 2) = t122;
+            FPC_D(2, 1, 2) = t212;
+            FPC_D(2, 2, 1) = t221;
         }
-        FPC_D(1, 2, 2) = t122;
-        FPC_D(2, 1, 2) = t212;
-        FPC_D(2, 2, 1) = t221;
     }
 
     // order 6: attractor from post-collision second and fourth moments
@@ -432,7 +456,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
             A222 = (t - ninth * drho) * (third * inv_rho);
         }
         if constexpr (R1) {
-            FPC_D(2, 2, 2) = A222;
+            FPC_D(2, 2, 2) = FORCE ? fmaR(R(0.5), s222, A222) : A222;
         } else {
             R t222 = fmaR(rt.om[26], A222, rt.keep[26] * FPC_D(2, 2, 2));
             if (FORCE) t222 = fmaR(rt.src[26], s222, t222);
@@ -441,7 +465,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     }
 
     // ---- Steps 4+5: back to populations (passes in reverse order) ----
-    if constexpr (R1) {
+    if constexpr (ODD0) {
         // x lines at fixed (n, p); inputs of total order 3 or 5 are zero
 #define FPC_INVC(n, p, Z0, Z1, Z2)                                                                        \
     inv3z<R, r1(n) * r1(p) == 0.0, Z0, Z1, Z2>(g[3 * (n) + 9 * (p)], g[1 + 3 * (n) + 9 * (p)],           \

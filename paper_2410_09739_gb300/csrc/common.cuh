@@ -19,10 +19,10 @@ namespace fpc {
 // FP with the learned shear-rate correction, FP with the Smagorinsky eddy
 // viscosity (van Driest damped) in the shear rates.  MODE_FP_R1 and
 // MODE_EQ_R1 are the FP and MCM modes in the paper's default setting, every
-// rate of order >= 3 equal to 1 and no body force: the post-collision moments
-// of orders 3-6 are then their attractors (kappa + 1 (kappa^Mv - kappa) =
-// kappa^Mv, no source), so the pre-collision moments of those orders are not
-// formed at all.
+// rate of order >= 3 equal to 1: the post-collision moments of orders 3-6 are
+// then their attractors plus half their sources (kappa + 1 (kappa^Mv - kappa)
+// + (1 - 1/2) sigma), with no grouping; without force the pre-collision
+// moments of those orders are not formed at all.
 enum { MODE_FP = 0, MODE_EQ = 1, MODE_LEARNED = 2, MODE_SMAG = 3, MODE_FP_R1 = 4, MODE_EQ_R1 = 5 };
 
 // FP or MCM attractors with the full register-cap / pipelined / paired variant set.

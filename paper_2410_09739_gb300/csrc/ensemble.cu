@@ -114,16 +114,10 @@ template <int MODE>
 static cudaError_t go_mode(int odd, int force, const EnsArgs& a, int block, int minb, int grid, int variant,
                            cudaStream_t st)
 {
-    if constexpr (r1_mode(MODE)) {  // unit rates of orders >= 3: no body force by construction
-        if (force) return cudaErrorInvalidValue;
-        return odd ? go<true, false, MODE>(a, block, minb, grid, variant, st)
-                   : go<false, false, MODE>(a, block, minb, grid, variant, st);
-    } else {
-        if (odd) return force ? go<true, true, MODE>(a, block, minb, grid, variant, st)
-                              : go<true, false, MODE>(a, block, minb, grid, variant, st);
-        return force ? go<false, true, MODE>(a, block, minb, grid, variant, st)
-                     : go<false, false, MODE>(a, block, minb, grid, variant, st);
-    }
+    if (odd) return force ? go<true, true, MODE>(a, block, minb, grid, variant, st)
+                          : go<true, false, MODE>(a, block, minb, grid, variant, st);
+    return force ? go<false, true, MODE>(a, block, minb, grid, variant, st)
+                 : go<false, false, MODE>(a, block, minb, grid, variant, st);
 }
 
 cudaError_t launch_ens_step(int odd, int force, int mode, const EnsArgs& a, int block, int minb, int grid,

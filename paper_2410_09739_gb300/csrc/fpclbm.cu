@@ -197,14 +197,14 @@ BoxGeom geom_of(const fpclbm* h, const Box& b)
 bool has_force(const fpclbm* h) { return h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0; }
 
 // Collision mode of the step kernel.  A box or ensemble in the FP or MCM mode whose rates of
-// orders 3-6 (Step 3 indices 10..26) are all exactly 1 and that carries no body force takes
-// the unit-rate variant, which never forms the pre-collision moments of those orders.
+// orders 3-6 (Step 3 indices 10..26) are all exactly 1 takes the unit-rate variant, which sets
+// those moments to their attractors plus half their sources (and, without force, never forms
+// their pre-collision values).
 int mode_of(const fpclbm* h)
 {
     if (h->diffusion == FPCLBM_DIFF_FP_LEARNED) return MODE_LEARNED;
     if (h->diffusion == FPCLBM_DIFF_FP_SMAGORINSKY) return MODE_SMAG;
     const int m = h->diffusion == FPCLBM_DIFF_EQUILIBRIUM ? MODE_EQ : MODE_FP;
-    if (has_force(h)) return m;
     for (int j = 10; j < 27; ++j)
         if (h->omega[j] != 1.0) return m;
     return m == MODE_EQ ? MODE_EQ_R1 : MODE_FP_R1;

@@ -1,12 +1,18 @@
-// step_fp16.cu -- step-kernel instantiations for __half storage, float arithmetic.
+// step_fp16.cu -- step-kernel instantiations for __half storage, float arithmetic: the
+// even parity here, the odd parity in step_fp16_odd.cu (two translation units
+// compile in parallel).
 #include "step_kernel.cuh"
 
 namespace fpc {
 
+cudaError_t launch_step_fp16_odd(int bc, int force, int mode, const StepArgs<float>& a, const StepLaunch& cfg,
+                             cudaStream_t st);
+
 cudaError_t launch_step_fp16(int odd, int bc, int force, int mode, const StepArgs<float>& a, const StepLaunch& cfg,
                           cudaStream_t st)
 {
-    return step_dispatch<__half, float>(odd, bc, force, mode, a, cfg, st);
+    if (odd) return launch_step_fp16_odd(bc, force, mode, a, cfg, st);
+    return step_by_bc<__half, float, false>(bc, force, mode, a, cfg, st);
 }
 
 }  // namespace fpc

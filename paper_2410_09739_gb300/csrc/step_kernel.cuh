@@ -264,12 +264,8 @@ cudaError_t step_by_mode(int mode, const StepArgs<R>& a, const StepLaunch& cfg, 
     switch (mode) {
         case MODE_FP: return step_by_minb<S, R, ODD, BC, FORCE, MODE_FP>(a, cfg, st);
         case MODE_EQ: return step_by_minb<S, R, ODD, BC, FORCE, MODE_EQ>(a, cfg, st);
-        case MODE_FP_R1:  // unit rates of orders >= 3 without body force
-            if constexpr (!FORCE) return step_by_minb<S, R, ODD, BC, FORCE, MODE_FP_R1>(a, cfg, st);
-            break;
-        case MODE_EQ_R1:
-            if constexpr (!FORCE) return step_by_minb<S, R, ODD, BC, FORCE, MODE_EQ_R1>(a, cfg, st);
-            break;
+        case MODE_FP_R1: return step_by_minb<S, R, ODD, BC, FORCE, MODE_FP_R1>(a, cfg, st);  // unit rates, orders >= 3
+        case MODE_EQ_R1: return step_by_minb<S, R, ODD, BC, FORCE, MODE_EQ_R1>(a, cfg, st);
         case MODE_LEARNED:  // periodic and channel boxes (the closure's training data come from them)
             if constexpr (BC == BC_PERIODIC || BC == BC_WALLS_Y)
                 return step_by_minb<S, R, ODD, BC, FORCE, MODE_LEARNED>(a, cfg, st);

@@ -89,23 +89,26 @@ def test_one_step_fp64_random_populations(shape, bc, force, mode):
 @pytest.mark.parametrize("shape", [(3, 3, 3), (17, 9, 5)])
 @pytest.mark.parametrize("bc", [0, 1, 2, 3])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_one_step_fp64_unit_high_rates(shape, bc, mode):
-    """Rates of orders 3-6 exactly 1 and no force (the paper's default) select the unit-rate
-    kernels, which set those moments straight to their attractors; random populations far from
-    equilibrium, random shear and bulk rates, every boundary kind (closed box with a moving lid)."""
+@pytest.mark.parametrize("force", [False, True])
+def test_one_step_fp64_unit_high_rates(shape, bc, mode, force):
+    """Rates of orders 3-6 exactly 1 (the paper's default) select the unit-rate kernels, which set
+    those moments to their attractors plus half their sources; random populations far from
+    equilibrium, random shear and bulk rates, every boundary kind (closed box with a moving lid),
+    with and without a body force."""
     nx, ny, nz = shape
-    seed = 500 + nx + bc * 7 + mode
+    seed = 500 + nx + bc * 7 + mode + 11 * force
     f0 = W.random_populations(nx * ny * nz, seed).reshape(27, nz, ny, nx)
     om = random_rates(seed)
     om[10:] = 1.0
     uw = 0.03 if bc == 2 else 0.0
-    with make(nx, ny, nz, "fp64", bc, omega=om, mode=mode) as lat:
+    Fv = (2e-3, -1e-3, 1.5e-3) if force else (0, 0, 0)
+    with make(nx, ny, nz, "fp64", bc, Fv, omega=om, mode=mode) as lat:
         if bc == 2:
             lat.set_wall_velocity(uw)
         lat.set_populations(f0)
         lat.step(1)
         got = lat.get_populations()
-    ref = O.step(f0, bc=bc, omega=om, mode=mode, uw=(uw, 0.0, 0.0))
+    ref = O.step(f0, bc=bc, F=Fv, omega=om, mode=mode, uw=(uw, 0.0, 0.0))
     assert rel(got, ref) <= 1e-12
 
 
@@ -314,9 +317,9 @@ def test_launch_query_names_the_collision_mode():
         got = lat.launch()
         assert got["mode"] == 4  # default rates, no force: FP with unit rates of orders 3-6
         assert got["variant"] in (0, 1, 2) and got["block"] in (128, 256) and 1 <= got["minb"] <= 4
-        lat.set_force(1e-5, 0, 0)  # the general kernels
+        lat.set_force(1e-5, 0, 0)  # a force keeps the unit-rate kernels (half the sources)
         lat.step(2)
-        assert lat.launch()["mode"] == 0
+        assert lat.launch()["mode"] == 4
         lat.set_force(0, 0, 0)
         om = O.rates(0.7)
         om[12] = 1.1  # one third-order rate off 1: general kernels again
