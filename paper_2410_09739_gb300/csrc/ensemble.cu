@@ -93,11 +93,38 @@ __global__ void __launch_bounds__(128, MINB) k_ens_pair(const EnsArgs a)
     }
 }
 
+// Resident blocks of 128 threads per SM of the even-step paired kernel with a given cap.
+template <bool FORCE, int MODE, int MINB>
+static int occ_even_pair()
+{
+    static int n = 0;  // benign race: every thread computes the same value
+    if (n == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ens_pair<false, FORCE, MODE, MINB>, 128, 0) !=
+                cudaSuccess ||
+            v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        n = v;
+    }
+    return n;
+}
+
 template <bool ODD, bool FORCE, int MODE>
 static cudaError_t go(const EnsArgs& a, int block, int minb, int grid, int variant, cudaStream_t st)
 {
     if (variant == 2) {
         if (block != 128 || a.tile_cells % (2 * block) != 0) return cudaErrorInvalidValue;
+        if constexpr (!ODD && !FORCE && r1_mode(MODE)) {
+            // the unit-rate even step without force (vector accesses, no neighbour table, no source
+            // terms) fits 5 blocks per SM without spilling;
+            // the persistent grid, sized by the tuner for the capped kernel, is scaled to match
+            const int o = minb == 3 ? occ_even_pair<FORCE, MODE, 3>() : occ_even_pair<FORCE, MODE, 4>();
+            const long long g5 = (long long)grid * occ_even_pair<FORCE, MODE, 5>() / o;
+            k_ens_pair<false, FORCE, MODE, 5><<<(unsigned)(g5 > 0 ? g5 : 1), block, 0, st>>>(a);
+            return cudaGetLastError();
+        }
         if (minb == 3)
             k_ens_pair<ODD, FORCE, MODE, 3><<<grid, block, 0, st>>>(a);
         else
