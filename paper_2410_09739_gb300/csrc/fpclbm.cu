@@ -399,7 +399,10 @@ int autotune(fpclbm* h)
             }
         for (int minb : {3, 4}) {  // paired variant: 3 or 4 blocks of 128 threads per SM
             const int per_sm = ens_max_blocks_per_sm(128, minb, mode_of(h), 2);
-            for (int mult : {1, 2}) cands.push_back({128, minb, h->sm_count * per_sm * mult, 2});
+            // oversubscribed grids let the block scheduler even out boxes of different cost, up to
+            // one tile per block
+            for (int mult : {1, 2, 4, 8, 16}) cands.push_back({128, minb, h->sm_count * per_sm * mult, 2});
+            cands.push_back({128, minb, (int)h->ntiles, 2});
         }
     } else if (fp32_math) {
         for (int minb : {2, 3, 4})
