@@ -306,14 +306,17 @@ __device__ __forceinline__ void update_pair_even(S* __restrict__ buf, const Cell
 // second cell's address is the first one's plus 1, minus nx where the
 // second cell's neighbour column wraps (x + 2 = nx for a neighbour at x + 1
 // of the first cell, x = 0 for one at x - 1); a bounce-back redirect stays
-// within the cells' own slots (plus 1).  Periodic x only (no closed box).
+// within the cells' own slots (plus 1).  In the closed box the x walls give
+// the two cells different tests for e_x != 0, so there the second cell's
+// address is formed from its own test.  Not for the half channel.
 template <typename S, int BC, bool FORCE, int MODE>
 __device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const CellGeom& G, unsigned t,
                                                     const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5,
                                                     f2 om6, f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0),
                                                     f2 lid6z = f2(0.0))
 {
-    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_WALLS_Y_LID, "periodic x, walls in y only");
+    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_WALLS_Y_LID || BC == BC_BOX_LID,
+                  "no symmetry plane");
     const unsigned stride = G.stride;
     unsigned c = 2 * t;
     f2 g[27];
@@ -329,9 +332,16 @@ __device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const C
             if (ix == 1) {
                 g[s] = Store2<S>::ld(p);
             } else {  // the read is at x - e_x: x + 1 for ix = 0, x - 1 for ix = 2
-                const int w = inside<BC>(n, ix, iy, iz) ? (ix == 0 ? wp : wm) : 0;
                 g[s].v.x = Store<S>::ld(p);
-                g[s].v.y = Store<S>::ld(p + 1 + w);
+                if constexpr (BC == BC_BOX_LID) {  // x walls: the second cell's source has its own test
+                    const int x2 = ix == 0 ? x + 2 : x;
+                    const bool in2 = n.yin[iy] && n.zin[iz] && x2 < G.nx;
+                    g[s].v.y = Store<S>::ld(in2 ? buf + (size_t)(26 - s) * stride + ((unsigned)x2 + n.yz[iy][iz])
+                                                : buf + (size_t)s * stride + (c + 1));
+                } else {
+                    const int w = inside<BC>(n, ix, iy, iz) ? (ix == 0 ? wp : wm) : 0;
+                    g[s].v.y = Store<S>::ld(p + 1 + w);
+                }
             }
         }
     }
@@ -350,9 +360,17 @@ __device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const C
         if (ix == 1) {
             Store2<S>::st(p, g[s]);
         } else {  // the write is at x + e_x: x + 1 for ix = 2, x - 1 for ix = 0
-            const int w = inside<BC>(n, 2 - ix, 2 - iy, 2 - iz) ? (ix == 2 ? wp : wm) : 0;
             Store<S>::st(p, g[s].v.x);
-            Store<S>::st(p + 1 + w, g[s].v.y);
+            if constexpr (BC == BC_BOX_LID) {
+                const int x2 = ix == 2 ? x + 2 : x;  // the second cell writes to x + 1 + e_x
+                const bool in2 = n.yin[2 - iy] && n.zin[2 - iz] && x2 < G.nx;
+                Store<S>::st(in2 ? buf + (size_t)s * stride + ((unsigned)x2 + n.yz[2 - iy][2 - iz])
+                                 : buf + (size_t)(26 - s) * stride + (c + 1),
+                             g[s].v.y);
+            } else {
+                const int w = inside<BC>(n, 2 - ix, 2 - iy, 2 - iz) ? (ix == 2 ? wp : wm) : 0;
+                Store<S>::st(p + 1 + w, g[s].v.y);
+            }
         }
     }
 }

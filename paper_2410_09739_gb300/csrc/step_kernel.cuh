@@ -209,8 +209,9 @@ cudaError_t step_go_pair(const StepArgs<float>& a, cudaStream_t st)
     constexpr bool LID = BC == BC_WALLS_Y_LID || BC == BC_BOX_LID;
     constexpr int BLOCKS = (ODD || FORCE || LID) ? 2 * MINB : 2 * MINB + 1;
     const unsigned grid = (half + 127) / 128;
-    // neighbouring cells on the odd step: x periodic and nx even (rows hold whole pairs)
-    constexpr bool ADJ_OK = ODD && (BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_WALLS_Y_LID);
+    // neighbouring cells on the odd step: nx even (rows hold whole pairs), no symmetry plane; the
+    // closed box only with fp32 storage (its per-cell x-wall tests spill with 16-bit unpacking)
+    constexpr bool ADJ_OK = ODD && BC != BC_HALF_CHANNEL && (BC != BC_BOX_LID || sizeof(S) == 4);
     if (ADJ_OK && (a.nx & 1) == 0)
         k_step_pair<S, ODD, BC, FORCE, MODE, BLOCKS, ADJ_OK><<<grid, 128, 0, st>>>(pair_args(a), half);
     else
