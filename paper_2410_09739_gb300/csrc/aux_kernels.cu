@@ -21,13 +21,17 @@ const int kSlotOfAlpha[27] = {FPC_SLOT(0),  FPC_SLOT(1),  FPC_SLOT(2),  FPC_SLOT
 #undef FPC_SLOT
 
 struct AlphaMap {
-    int slot[27];
+    int slot[27];   // tensor slot of each alpha
+    int alpha[27];  // alpha of each tensor slot
 };
 
 static AlphaMap alpha_map()
 {
     AlphaMap m;
-    for (int a = 0; a < 27; ++a) m.slot[a] = kSlotOfAlpha[a];
+    for (int a = 0; a < 27; ++a) {
+        m.slot[a] = kSlotOfAlpha[a];
+        m.alpha[kSlotOfAlpha[a]] = a;
+    }
     return m;
 }
 
@@ -36,6 +40,16 @@ static AlphaMap alpha_map()
 // product (w1x + ax)(w1y + ay)(w1z + az) - w1x w1y w1z is expanded so that
 // only small terms are summed.  (Equal to C(u)^-1 kappa^eq with kappa^eq the
 // Maxwellian central moments (1, 0, cs^2) per axis.)
+//
+// The arithmetic follows the storage type.  This GPU's fp64 pipe is a small
+// fraction of its fp32 one, and the fp64 form below took ~220 fp64
+// instructions per cell, which made the kernel fp64-bound (5.7 ms for 256^3)
+// rather than bound by reading the fields.  FP64 storage keeps it.  FP32
+// storage forms the three per-axis factors w1 + dphi in fp64 and then
+// g = rho X Y Z - w with one fma per slot: the cancellation against w costs at
+// most ~8 of fp64's 53 bits, far below the 24 bits stored.  16-bit storage
+// evaluates the expanded form in fp32 (a few fp32 ulps of error against at
+// most 11 stored bits).
 template <typename S>
 __global__ void k_init_eq(BoxGeom b, const double* rho, const double* ux, const double* uy, const double* uz,
                           unsigned c0, unsigned n)
@@ -43,6 +57,50 @@ __global__ void k_init_eq(BoxGeom b, const double* rho, const double* ux, const 
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned cell = c0 + i;
+    if constexpr (std::is_same<S, float>::value) {
+        const double r = rho[i], u[3] = {ux[i], uy[i], uz[i]};
+        double X[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double v = u[d], v2 = v * v;
+            X[d][0] = w1(0) + 0.5 * (v2 - v);
+            X[d][1] = w1(1) - v2;
+            X[d][2] = w1(2) + 0.5 * (v2 + v);
+        }
+        float* buf = static_cast<float*>(b.buf);
+#pragma unroll
+        for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
+            for (int iy = 0; iy < 3; ++iy) {
+                const double yz = X[1][iy] * X[2][iz];
+#pragma unroll
+                for (int ix = 0; ix < 3; ++ix) {
+                    const int s = ix + 3 * iy + 9 * iz;
+                    buf[(size_t)s * b.stride + cell] = (float)(r * (X[0][ix] * yz) - wslot(s));
+                }
+            }
+        return;
+    } else if constexpr (!std::is_same<S, double>::value) {
+        const float dr = (float)(rho[i] - 1.0), u[3] = {(float)ux[i], (float)uy[i], (float)uz[i]};
+        float dphi[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float v = u[d], v2 = v * v;
+            dphi[d][0] = 0.5f * (v2 - v);
+            dphi[d][1] = -v2;
+            dphi[d][2] = 0.5f * (v2 + v);
+        }
+        S* buf = static_cast<S*>(b.buf);
+#pragma unroll
+        for (int s = 0; s < 27; ++s) {
+            const int ix = s % 3, iy = (s / 3) % 3, iz = s / 9;
+            const float A = (float)w1(ix), B = (float)w1(iy), C = (float)w1(iz);
+            const float a = dphi[0][ix], bb = dphi[1][iy], c = dphi[2][iz];
+            const float dprod = a * (B + bb) * (C + c) + A * (bb * (C + c) + B * c);
+            Store<S>::st(buf + (size_t)s * b.stride + cell, dr * ((A + a) * (B + bb) * (C + c)) + dprod);
+        }
+        return;
+    }
     const double r = rho[i], u[3] = {ux[i], uy[i], uz[i]};
     double dphi[3][3];
     for (int d = 0; d < 3; ++d) {
@@ -63,15 +121,40 @@ __global__ void k_init_eq(BoxGeom b, const double* rho, const double* ux, const 
     }
 }
 
+// Density and half-force velocity (Step 7) of every cell, in fp64.  For fp32
+// and 16-bit storage the 27 deviations are summed in fp32 with compensation
+// (sum2_add), which gives the fp64 sums in all but the last bits at fp32 cost,
+// and the three divisions by rho become one reciprocal: the fp64 form below
+// made the kernel fp64-bound on this GPU.  FP64 storage keeps the fp64 form.
 template <typename S>
 __global__ void k_moments(BoxGeom b, int parity, double Fx, double Fy, double Fz, double* rho, double* ux,
                           double* uy, double* uz, unsigned c0, unsigned n)
 {
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if constexpr (!std::is_same<S, double>::value) {
+        float g[27];
+        load_cell<S>(b, parity, c0 + i, g);
+        float ds = 0.f, dc = 0.f, xs = 0.f, xc = 0.f, ys = 0.f, yc = 0.f, zs = 0.f, zc = 0.f;
+#pragma unroll
+        for (int s = 0; s < 27; ++s) {
+            const int ex = s % 3 - 1, ey = (s / 3) % 3 - 1, ez = s / 9 - 1;
+            sum2_add(ds, dc, g[s]);
+            if (ex != 0) sum2_add(xs, xc, ex > 0 ? g[s] : -g[s]);
+            if (ey != 0) sum2_add(ys, yc, ey > 0 ? g[s] : -g[s]);
+            if (ez != 0) sum2_add(zs, zc, ez > 0 ? g[s] : -g[s]);
+        }
+        const double r = 1.0 + ((double)ds + (double)dc), inv = 1.0 / r;
+        if (rho) rho[i] = r;
+        if (ux) ux[i] = ((double)xs + (double)xc + 0.5 * Fx) * inv;
+        if (uy) uy[i] = ((double)ys + (double)yc + 0.5 * Fy) * inv;
+        if (uz) uz[i] = ((double)zs + (double)zc + 0.5 * Fz) * inv;
+        return;
+    }
     double g[27];
     load_cell<S>(b, parity, c0 + i, g);
     double dr = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
     for (int s = 0; s < 27; ++s) {
         dr += g[s];
         jx += (s % 3 - 1) * g[s];
@@ -92,10 +175,8 @@ __global__ void k_get_pops(BoxGeom b, AlphaMap am, int parity, double* out, unsi
     if (i >= n) return;
     double g[27];
     load_cell<S>(b, parity, c0 + i, g);
-    for (int a = 0; a < 27; ++a) {
-        const int s = am.slot[a];
-        out[(size_t)a * ld + i] = wslot(s) + g[s];
-    }
+#pragma unroll
+    for (int s = 0; s < 27; ++s) out[(size_t)am.alpha[s] * ld + i] = wslot(s) + g[s];
 }
 
 template <typename S>
@@ -107,10 +188,8 @@ __global__ void k_get_pops_at(BoxGeom b, AlphaMap am, int parity, const unsigned
     if (cell >= b.ncells) return;
     double g[27];
     load_cell<S>(b, parity, cell, g);
-    for (int a = 0; a < 27; ++a) {
-        const int s = am.slot[a];
-        out[(size_t)a * n + i] = wslot(s) + g[s];
-    }
+#pragma unroll
+    for (int s = 0; s < 27; ++s) out[(size_t)am.alpha[s] * n + i] = wslot(s) + g[s];
 }
 
 template <typename S>
@@ -149,6 +228,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(BoxGeom b, int pa
         double g[27];
         load_cell<S>(b, parity, cell, g);
         double dr = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
         for (int s = 0; s < 27; ++s) {
             dr += g[s];
             jx += (s % 3 - 1) * g[s];
