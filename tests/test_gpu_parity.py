@@ -68,6 +68,44 @@ def test_init_matches_oracle_equilibrium(shape):
     assert rel(got, O.init_equilibrium(rho, ux, uy, uz)) < 1e-14
 
 
+@pytest.mark.parametrize("prec,unit,slack", [("fp32", 2.0 ** -24, 1e-14), ("fp16", 2.0 ** -11, 1e-7),
+                                             ("bf16", 2.0 ** -8, 1e-7)])
+@pytest.mark.parametrize("shape", [(5, 4, 3), (33, 7, 6)])
+def test_init_reduced_precision_is_rounded_equilibrium(shape, prec, unit, slack):
+    """Each stored deviation is the oracle's equilibrium deviation rounded once to the storage type:
+    |g_stored - g| <= unit |g| (round to nearest), plus a slack for the oracle's own fp64 LU
+    rounding (fp32) or for the fp32 arithmetic of the 16-bit init and fp16 subnormals (16-bit)."""
+    nx, ny, nz = shape
+    rho, ux, uy, uz = W.random_fields(nx, ny, nz, seed=15, u_amp=0.1)
+    with make(nx, ny, nz, prec) as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        got = lat.get_populations()
+    g = O.init_equilibrium(rho, ux, uy, uz) - W_REST[:, None, None, None]
+    err = np.abs((got - W_REST[:, None, None, None]) - g)
+    assert np.all(err <= unit * np.abs(g) + slack), float(np.max(err - unit * np.abs(g)))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_moments_reduced_precision_are_fp64_sums(prec, bc):
+    """The moments of fp32 / 16-bit storage sum the stored deviations in fp32 with compensation: the
+    result must equal the oracle's fp64 density and half-force velocity (Step 7) of the same stored
+    populations up to rounding (a plain fp32 sum would be off by ~1e-9; the compensated sums and the
+    fp64 ones agree to ~1e-16, so 1e-12 leaves a wide margin).  Odd step count: the moments read the
+    AA odd layout."""
+    nx, ny, nz = 17, 9, 5
+    Fv = (1e-4, -5e-5, 2e-5)
+    rho, ux, uy, uz = W.random_fields(nx, ny, nz, seed=16, u_amp=0.08)
+    with make(nx, ny, nz, prec, bc, Fv, tau=0.7) as lat:
+        lat.init_fields(rho, ux, uy, uz)
+        lat.step(3)
+        got = lat.moments()
+        f = lat.get_populations()
+    ref = O.moments(f, Fv)
+    for x, y in zip(got, ref):
+        assert np.max(np.abs(x.reshape(y.shape) - y)) <= 1e-12
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("force", [False, True])
