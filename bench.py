@@ -244,8 +244,17 @@ def cpu_oracle_sample_2d(L, tau, U, target_s=15.0):
             "sample": "%d x %d shear layers (D2Q9), %d FP64 oracle steps, %.1f s" % (n, n, done, el)}
 
 
+def tgv_workload(n, tau):
+    """The TGV workload's name in the config of both arms."""
+    return "TGV Re=1600 %d^3 periodic, u0=0.05, tau=%.6f" % (n, tau)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
+        return
+    if args.workload != "tgv":
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm (the FP64 CPU oracle) is timed "
+                          "on the TGV workload only; run it without --workload"}), flush=True)
         return
     n, u0 = args.size, 0.05
     tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
@@ -269,7 +278,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "TGV Re=1600 %d^3 periodic (slab sample)" % n, "precision": "fp64",
+        "config": {"workload": tgv_workload(n, tau), "precision": "fp64", "sample": sample,
                    "l2": "inputs larger than L2 not applicable (CPU)"},
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": planes, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -317,7 +326,7 @@ def setup(args, F, prec, stream):
         lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_PERIODIC, stream=stream)
         lat.set_params(tau)
         flds = W.tgv(n, u0)
-        cfg = {"workload": "TGV Re=1600 %d^3 periodic, u0=0.05, tau=%.6f" % (n, tau)}
+        cfg = {"workload": tgv_workload(n, tau)}
     elif args.workload == "channel":
         nx, ny, nz, u_star = 384, 192, 192, 0.005
         H = ny / 2
