@@ -109,7 +109,9 @@ FPCLBM_API int fpclbm_create_ensemble(fpclbm_t* out, int n_boxes, const int* dim
 /* Initialise every cell to the equilibrium of the given density and velocity:
  * f = C(u)^-1 kappa^eq(rho, u), kappa^eq the Maxwellian central moments (the
  * paper gives no initial condition; this is the equilibrium of Sec. 3 at the
- * given fields).  Resets the step counter to 0.  Errors: ARG, STATE, CUDA. */
+ * given fields).  Each stored deviation f - w is that equilibrium rounded
+ * once to the storage type (for 16-bit storage after an fp32 evaluation, a few
+ * fp32 ulps away).  Resets the step counter to 0.  Errors: ARG, STATE, CUDA. */
 FPCLBM_API int fpclbm_init_fields(fpclbm_t h, const double* rho, const double* ux, const double* uy,
                        const double* uz, int on_device);
 
@@ -171,7 +173,10 @@ FPCLBM_API int fpclbm_step(fpclbm_t h, long long n);
 
 /* Density and half-force velocity of every cell (Appendix D Step 7:
  * rho = sum f, rho u = sum f e + F/2).  Outputs of N doubles each; any of the
- * four pointers may be NULL to skip it.  Errors: ARG, STATE, CUDA. */
+ * four pointers may be NULL to skip it.  The values are the fp64 sums of the
+ * stored populations (for fp32 and 16-bit storage formed by compensated fp32
+ * summation, equal to the fp64 sums up to their last bits).  Errors: ARG,
+ * STATE, CUDA. */
 FPCLBM_API int fpclbm_moments(fpclbm_t h, double* rho, double* ux, double* uy, double* uz, int on_device);
 
 /* Global diagnostics reduced in fp64 on the device: out[0] = sum rho,

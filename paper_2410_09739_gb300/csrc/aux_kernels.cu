@@ -1,6 +1,7 @@
 // aux_kernels.cu -- initialisation, field export, population I/O and fp64
-// diagnostics of one box.  None of these is on the time-step hot path; they
-// compute in fp64 whatever the storage precision.
+// diagnostics of one box.  None of these is on the time-step hot path.  Fields
+// and populations cross the boundary in fp64; the arithmetic is fp64 except
+// where k_init_eq and k_moments state otherwise for fp32 and 16-bit storage.
 #include "aux.cuh"
 #include "internal.h"
 
