@@ -9,6 +9,7 @@ import os
 import numpy as np
 import pytest
 
+from dispersion import shear_wave_discrete_rate
 from oracle import oracle2d as O2
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -162,6 +163,30 @@ def test_shear_wave_viscosity(tau):
         ts.append(t)
     nu = CS2 * (tau - 0.5)
     assert abs(_decay_rate(amps, ts) / (nu * k * k) - 1) < 0.01
+
+
+@pytest.mark.parametrize("tau,bulk,drift", [(0.6, 0.0, 0.0), (1.0, 0.0, 0.0), (0.6, 0.0, 0.3), (0.7, 1.5, 0.2)])
+def test_shear_wave_decay_matches_discrete_dispersion(tau, bulk, drift):
+    """The 2D shear wave decays exactly as the scheme's discrete dispersion relation says (the same
+    3x3 map of j, m_11, m_12 as in 3D: shear rates omega_4 = omega_5 = 1/tau, third-order rates
+    omega_6 = omega_7 = 1 or 3 drift), whatever the bulk rate."""
+    om = O2.rates(tau, bulk, drift)
+    for n in (16, 32):
+        k = 2 * math.pi / n
+        y = np.arange(n)
+        ux = 1e-4 * np.sin(k * y)[:, None] * np.ones((1, 2))
+        f = O2.init_equilibrium(np.ones((n, 2)), ux, np.zeros((n, 2)))
+        chunk = 20 * (n // 16) ** 2
+        amps, ts = [], []
+        for i in range(16):
+            f = O2.run(f, chunk, omega=om)
+            if i >= 3:  # past the decay of the non-hydrodynamic modes
+                _, u, _ = O2.moments(f)
+                amps.append(2 / n * u[:, 0] @ np.sin(k * y))
+                ts.append(chunk * (i + 1))
+        rate = _decay_rate(np.abs(amps), ts)
+        exact = shear_wave_discrete_rate(n, tau, float(om[6]))
+        assert abs(rate / exact - 1) < 3e-8, (n, rate, exact)
 
 
 @pytest.mark.parametrize("bulk", [0.5, 1.0, 1.6])

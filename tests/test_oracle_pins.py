@@ -15,6 +15,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from dispersion import shear_wave_discrete_rate
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 CS2 = 1.0 / 3.0
@@ -480,30 +481,10 @@ def test_shear_wave_viscosity(tau):
     assert abs(rate / (nu * k * k) - 1) < 0.01
 
 
-def _shear_wave_discrete_rate(n, tau, r3):
-    """Exact per-step decay rate of a small shear wave u_x = U sin(k y), k = 2 pi / n, under the
-    linearised scheme (von Neumann analysis of collide-and-stream).
-
-    With the flow in x and variation in y only, sum the populations over e_z and weight them by e_x.
-    The three moments j = m_100, P = m_110, Q = m_120 of that x-odd part evolve on their own:
-    collision keeps j (no force), relaxes P (the central kappa_110, attractor 0) at the shear rate
-    omega = 1/tau and relaxes Q (raw m_120 = kappa_120 + c_s^2 j to first order in u, third-order
-    attractor 0) at the third-order rate r3; streaming moves the e_y = +-1 parts by one cell, a factor
-    exp(-+ i k) on a Fourier mode.  The wave decays with the largest eigenvalue lambda of the 3x3
-    step matrix: rate = -ln |lambda|.  For r3 = 1, rate = nu k^2 (1 + (1 - tau)^2 k^2 / 3 + O(k^4)),
-    nu = c_s^2 (tau - 1/2)."""
-    k = 2 * math.pi / n
-    c, s = math.cos(k), math.sin(k)
-    collide = np.array([[1, 0, 0], [0, 1 - 1 / tau, 0], [r3 * CS2, 0, 1 - r3]], dtype=complex)
-    stream = np.array([[1, -1j * s, -(1 - c)], [0, c, -1j * s], [0, -1j * s, c]], dtype=complex)
-    lam = np.linalg.eigvals(stream @ collide)
-    return -math.log(float(np.max(np.abs(lam))))
-
-
 @pytest.mark.parametrize("tau,drift", [(0.6, 0.0), (0.8, 0.0), (1.0, 0.0), (0.6, 0.3), (0.7, 0.2)])
 def test_shear_wave_decay_matches_discrete_dispersion(tau, drift):
     """The measured decay of a shear wave equals the scheme's exact discrete dispersion relation
-    (_shear_wave_discrete_rate) for the shear rate 1/tau (Eq. transportcoeff3DFPCLBM) and the
+    (dispersion.shear_wave_discrete_rate) for the shear rate 1/tau (Eq. transportcoeff3DFPCLBM) and the
     third-order rate (1 for drift 0, the paper's default; 3 omega_FP otherwise, Sec. 3).  The
     rate-1 relation misses by ~1e-3 when the third-order rates are 0.9, so this fixes those rates
     too, which the leading-order viscosity test cannot.  For drift 0 the continuum error
@@ -528,7 +509,7 @@ def test_shear_wave_decay_matches_discrete_dispersion(tau, drift):
                 amps.append(2 / n * np.dot(u[0, :, 0], s))
                 ts.append(chunk * (i + 1))
         rate = _decay_rate(np.abs(amps), ts)
-        exact = _shear_wave_discrete_rate(n, tau, r3)
+        exact = shear_wave_discrete_rate(n, tau, r3)
         # U = 1e-4: the nonlinear terms are O(U^2) relative
         assert abs(rate / exact - 1) < 3e-8, (n, rate, exact)
         errs[n] = rate / (nu * k * k) - 1
