@@ -26,3 +26,57 @@ def shear_wave_discrete_rate(n, tau, r3):
     stream = np.array([[1, -1j * s, -(1 - c)], [0, c, -1j * s], [0, -1j * s, c]], dtype=complex)
     lam = np.linalg.eigvals(stream @ collide)
     return -math.log(float(np.max(np.abs(lam))))
+
+
+def sound_wave_step_matrix_2d(n, omega, mcm=False):
+    """Linearised D2Q9 step of a plane sound wave along x (rho and u_x vary with x only, u_y = 0),
+    for the Fourier mode exp(i k x), k = 2 pi / n (von Neumann analysis of collide-and-stream).
+
+    Sum the populations over e_y with the weights 1 and e_y^2: the six moments m_00 = rho,
+    m_10 = j, m_20, m_02, m_12, m_22 of those two sums evolve on their own.  State: their deviations
+    (r, j, p, q, s, w) from the rest values (1, 0, c_s^2, c_s^2, 0, c_s^4).  Collision, to first
+    order around rest (u = j): the central kappa_20, kappa_02 differ from c_s^2 rho by
+    a = p - c_s^2 r, b = q - c_s^2 r; the bulk part a + b relaxes at omega_3 and the deviatoric part
+    a - b at omega_4 (2D Step 3 grouping), both toward 0; kappa_12 = m_12 - c_s^2 j relaxes at
+    omega_7 toward 0 and goes back to raw with + c_s^2 j; kappa_22 - c_s^4 rho = w - c_s^4 r relaxes
+    at omega_8 toward the linearised attractor: c_s^2 (a~ + b~) for the FP diffusion tensor
+    D' = kappa~_ij / rho (kappa^Mv_22 = kappa~_20 kappa~_02 / rho), 0 for the Maxwellian (MCM)
+    one.  Streaming moves the e_x = +-1 populations of both sums by one cell (factor exp(-+ i k)).
+    Returns the complex 6x6 matrix of one step; its eigenvalue pair of largest modulus is the
+    sound mode."""
+    k = 2 * math.pi / n
+    w3, w4, w7, w8 = (float(omega[i]) for i in (3, 4, 7, 8))
+
+    def collide(x):
+        r, j, p, q, s, w = x
+        a, b = p - CS2 * r, q - CS2 * r
+        bulk, dev = (1 - w3) * (a + b), (1 - w4) * (a - b)
+        at, bt = (bulk + dev) / 2, (bulk - dev) / 2
+        w0 = w - CS2 * CS2 * r
+        att = 0.0 if mcm else CS2 * bulk
+        return np.array([r, j, CS2 * r + at, CS2 * r + bt, (1 - w7) * (s - CS2 * j) + CS2 * j,
+                         CS2 * CS2 * r + w0 + w8 * (att - w0)], dtype=complex)
+
+    def stream(x):
+        r, j, p, q, s, w = x
+        ph = {e: np.exp(-1j * k * e) for e in (-1, 0, 1)}
+        a = {0: ph[0] * (r - p), 1: ph[1] * (p + j) / 2, -1: ph[-1] * (p - j) / 2}
+        b = {0: ph[0] * (q - w), 1: ph[1] * (w + s) / 2, -1: ph[-1] * (w - s) / 2}
+        return np.array([a[0] + a[1] + a[-1], a[1] - a[-1], a[1] + a[-1],
+                         b[0] + b[1] + b[-1], b[1] - b[-1], b[1] + b[-1]])
+
+    eye = np.eye(6)
+    C = np.stack([collide(eye[i]) for i in range(6)], axis=1)
+    S = np.stack([stream(eye[i]) for i in range(6)], axis=1)
+    return S @ C
+
+
+def prony_pair(xs):
+    """(p, q) of the recurrence x(t+2) = p x(t+1) - q x(t) that a complex-conjugate eigenvalue
+    pair lambda, lambda* gives (p = 2 Re lambda, q = |lambda|^2), least squares over a series."""
+    xs = np.asarray(xs)
+    A = np.stack([np.concatenate([xs[1:-1].real, xs[1:-1].imag]),
+                  -np.concatenate([xs[:-2].real, xs[:-2].imag])], axis=1)
+    b = np.concatenate([xs[2:].real, xs[2:].imag])
+    (p, q), *_ = np.linalg.lstsq(A, b, rcond=None)
+    return float(p), float(q)
