@@ -80,3 +80,49 @@ def prony_pair(xs):
     b = np.concatenate([xs[2:].real, xs[2:].imag])
     (p, q), *_ = np.linalg.lstsq(A, b, rcond=None)
     return float(p), float(q)
+
+
+def sound_wave_step_matrix_3d(n, omega, mcm=False):
+    """Linearised D3Q27 step of a plane sound wave along x (rho and u_x vary with x only), for the
+    Fourier mode exp(i k x), k = 2 pi / n (von Neumann analysis of collide-and-stream).
+
+    Sum the populations over (e_y, e_z) with the weights 1 and e_y^2 (equal to the e_z^2 sum by
+    symmetry): the six moments m_000 = rho, m_100 = j, m_200, m_020, m_120, m_220 of those two sums
+    evolve on their own.  The e_y^2 e_z^2 sum (m_022, m_122, m_222) is driven by them but does not
+    feed back, so it drops out of the sound mode.  State: the deviations (r, j, p, q, s, w) from the
+    rest values (1, 0, c_s^2, c_s^2, 0, c_s^4).  Collision, to first order around rest (u = j):
+    kappa_200 and kappa_020 = kappa_002 differ from c_s^2 rho by a = p - c_s^2 r, b = q - c_s^2 r;
+    the bulk part a + 2b relaxes at omega_7 and the deviatoric part a - b at omega_8 = omega_9
+    (3D Step 3 grouping), both toward 0; kappa_120 = m_120 - c_s^2 j relaxes at omega_10 toward 0
+    and goes back to raw with + c_s^2 j; kappa_220 - c_s^4 rho = w - c_s^4 r relaxes at omega_17
+    toward the linearised attractor, c_s^2 (a~ + b~) for the FP diffusion tensor
+    (kappa^Mv_220 = kappa~_200 kappa~_020 / rho with post-collision second moments) and 0 for the
+    Maxwellian (MCM) one.  Streaming moves the e_x = +-1 populations of both sums by one cell
+    (factor exp(-+ i k)).  Returns the complex 6x6 matrix of one step; its eigenvalue pair of
+    largest modulus is the sound mode.  All rates of one order must be equal (as set_params
+    makes them), since the plane wave does not see the grouping inside an order above the second."""
+    k = 2 * math.pi / n
+    wb, ws, r3, r4 = (float(omega[i]) for i in (7, 8, 10, 17))
+
+    def collide(x):
+        r, j, p, q, s, w = x
+        a, b = p - CS2 * r, q - CS2 * r
+        bulk, dev = (1 - wb) * (a + 2 * b), (1 - ws) * (a - b)
+        at, bt = (bulk + 2 * dev) / 3, (bulk - dev) / 3
+        d = w - CS2 * CS2 * r
+        att = 0.0 if mcm else CS2 * (at + bt)
+        return np.array([r, j, CS2 * r + at, CS2 * r + bt, (1 - r3) * (s - CS2 * j) + CS2 * j,
+                         CS2 * CS2 * r + d + r4 * (att - d)], dtype=complex)
+
+    def stream(x):
+        ph = {e: np.exp(-1j * k * e) for e in (-1, 0, 1)}
+        out = []
+        for m0, m1, m2 in ((x[0], x[1], x[2]), (x[3], x[4], x[5])):
+            a = {0: ph[0] * (m0 - m2), 1: ph[1] * (m2 + m1) / 2, -1: ph[-1] * (m2 - m1) / 2}
+            out += [a[0] + a[1] + a[-1], a[1] - a[-1], a[1] + a[-1]]
+        return np.array(out)
+
+    eye = np.eye(6)
+    C = np.stack([collide(eye[i]) for i in range(6)], axis=1)
+    S = np.stack([stream(eye[i]) for i in range(6)], axis=1)
+    return S @ C

@@ -15,7 +15,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from dispersion import shear_wave_discrete_rate
+from dispersion import prony_pair, shear_wave_discrete_rate, sound_wave_step_matrix_3d
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 CS2 = 1.0 / 3.0
@@ -518,6 +518,43 @@ def test_shear_wave_decay_matches_discrete_dispersion(tau, drift):
         assert abs(errs[16] / ((1 - tau) ** 2 * (2 * math.pi / 16) ** 2 / 3) - 1) < 0.02
     if tau == 1.0:
         assert abs(errs[16]) < 1e-4 and 12 < errs[16] / errs[32] < 20
+
+
+@pytest.mark.parametrize("tau,drift,bulk,mode", [(0.8, 0.0, None, O.EQ_MODE_FP), (0.6, 0.3, None, O.EQ_MODE_FP),
+                                              (0.8, 0.0, 0.5, O.EQ_MODE_FP), (0.8, 0.0, 0.5, O.EQ_MODE_MCM),
+                                              (0.7, 0.2, 0.6, O.EQ_MODE_MCM)])
+def test_sound_wave_matches_discrete_dispersion(tau, drift, bulk, mode):
+    """A plane sound wave rho = 1 + eps cos(k x) evolves with the acoustic eigenvalue pair of the
+    scheme's linearised step (dispersion.sound_wave_step_matrix_3d): the sound speed, the bulk and
+    shear grouping of the second-order moments with their rates (Eq. transportcoeff3DFPCLBM), the
+    third- and fourth-order rates and the fourth-order attractor with post-collision D' (Eqs.
+    Mvcmattractor3D, diffusion-tensor-parameter-3D) all enter.  Measured by a Prony fit of the
+    density's Fourier coefficient once the non-hydrodynamic modes have died out.  The FP and MCM
+    attractors give eigenvalues 2e-5 to 1e-3 apart, and the fit must match the mode that ran."""
+    om = O.rates(tau, drift).copy()
+    if bulk is not None:
+        om[7] = bulk
+    for n in (16, 24):
+        k = 2 * math.pi / n
+        x = np.arange(n)
+        rho = (1 + 1e-5 * np.cos(k * x)).reshape(1, 1, n)
+        zero = np.zeros((1, 1, n))
+        f = O.init_equilibrium(rho, zero, zero, zero)
+        xs = []
+        for t in range(300):
+            f = O.step(f, omega=om, mode=mode)
+            if t >= 60:
+                r, _, _, _ = O.moments(f)
+                xs.append(np.mean((r.reshape(-1) - 1) * np.exp(-1j * k * x)))
+        p, q = prony_pair(xs)
+        mcm = mode == O.EQ_MODE_MCM
+        lam = np.linalg.eigvals(sound_wave_step_matrix_3d(n, om, mcm=mcm))
+        lam = lam[np.argmax(np.abs(lam))]
+        assert abs(p - 2 * lam.real) < 1e-8 and abs(q - abs(lam) ** 2) < 1e-8, (n, p, q, lam)
+        other = np.linalg.eigvals(sound_wave_step_matrix_3d(n, om, mcm=not mcm))
+        other = other[np.argmax(np.abs(other))]
+        if n == 16:
+            assert abs(q - abs(other) ** 2) > 1e-6
 
 
 def test_sound_wave_attenuation_bulk_viscosity():
