@@ -86,43 +86,64 @@ def sound_wave_step_matrix_3d(n, omega, mcm=False):
     """Linearised D3Q27 step of a plane sound wave along x (rho and u_x vary with x only), for the
     Fourier mode exp(i k x), k = 2 pi / n (von Neumann analysis of collide-and-stream).
 
-    Sum the populations over (e_y, e_z) with the weights 1 and e_y^2 (equal to the e_z^2 sum by
-    symmetry): the six moments m_000 = rho, m_100 = j, m_200, m_020, m_120, m_220 of those two sums
-    evolve on their own.  The e_y^2 e_z^2 sum (m_022, m_122, m_222) is driven by them but does not
-    feed back, so it drops out of the sound mode.  State: the deviations (r, j, p, q, s, w) from the
-    rest values (1, 0, c_s^2, c_s^2, 0, c_s^4).  Collision, to first order around rest (u = j):
-    kappa_200 and kappa_020 = kappa_002 differ from c_s^2 rho by a = p - c_s^2 r, b = q - c_s^2 r;
-    the bulk part a + 2b relaxes at omega_7 and the deviatoric part a - b at omega_8 = omega_9
-    (3D Step 3 grouping), both toward 0; kappa_120 = m_120 - c_s^2 j relaxes at omega_10 toward 0
-    and goes back to raw with + c_s^2 j; kappa_220 - c_s^4 rho = w - c_s^4 r relaxes at omega_17
-    toward the linearised attractor, c_s^2 (a~ + b~) for the FP diffusion tensor
-    (kappa^Mv_220 = kappa~_200 kappa~_020 / rho with post-collision second moments) and 0 for the
-    Maxwellian (MCM) one.  Streaming moves the e_x = +-1 populations of both sums by one cell
-    (factor exp(-+ i k)).  Returns the complex 6x6 matrix of one step; its eigenvalue pair of
-    largest modulus is the sound mode.  All rates of one order must be equal (as set_params
-    makes them), since the plane wave does not see the grouping inside an order above the second."""
+    Sum the populations over (e_y, e_z) with the weights 1, e_y^2 (equal to the e_z^2 sum by
+    symmetry) and e_y^2 e_z^2: the nine moments m_000 = rho, m_100 = j, m_200; m_020, m_120, m_220;
+    m_022, m_122, m_222 of those three sums evolve on their own.  State: their deviations
+    (r, j, p, q, s, w, v, t, z) from the rest values (1, 0, c_s^2, c_s^2, 0, c_s^4, c_s^4, 0, c_s^6).
+    Collision, to first order around rest (u = j), in the chain order of Step 3:
+      * kappa_200 and kappa_020 = kappa_002 differ from c_s^2 rho by a = p - c_s^2 r, b = q - c_s^2 r;
+        the bulk part a + 2b relaxes at omega_7 and the deviatoric part a - b at omega_8 = omega_9,
+        both toward 0, giving a~, b~;
+      * kappa_120 = m_120 - c_s^2 j relaxes at omega_10 toward 0 (raw again: + c_s^2 j);
+      * kappa_220 - c_s^4 rho = w - c_s^4 r and kappa_022 - c_s^4 rho = v - c_s^4 r relax at omega_17
+        toward kappa~_200 kappa~_020 / rho and kappa~_020 kappa~_002 / rho, linearised
+        c_s^2 (a~ + b~) and 2 c_s^2 b~ (FP diffusion tensor, post-collision second moments);
+      * kappa_122 = m_122 - c_s^4 j relaxes at omega_23 toward
+        (2 / 5 rho)(kappa~_020 kappa~_102 + kappa~_002 kappa~_120), linearised (4/5) c_s^2 kappa~_120;
+      * kappa_222 - c_s^6 rho relaxes at omega_26 toward
+        (1 / 3 rho)(kappa~_200 kappa~_022 + kappa~_020 kappa~_202 + kappa~_002 kappa~_220), linearised
+        (c_s^4 (a~ + 2 b~) + c_s^2 (e~ + 2 d~)) / 3 with d~, e~ the post-collision deviations of
+        kappa_220 and kappa_022;
+    every attractor above second order is 0 (its Maxwellian value, relative to rest) for MCM.
+    Streaming moves the e_x = +-1 populations of the three sums by one cell (factor exp(-+ i k)).
+    The last three moments are driven by the first six without feeding back, so the sound mode
+    (the eigenvalue pair of largest modulus) does not depend on the fifth- and sixth-order
+    attractors; one step of the full matrix does.  All rates of one order must be equal (as
+    set_params makes them): the plane wave does not see the grouping inside an order above the
+    second.  Returns the complex 9x9 matrix of one step."""
     k = 2 * math.pi / n
-    wb, ws, r3, r4 = (float(omega[i]) for i in (7, 8, 10, 17))
+    wb, ws, r3, r4, r5, r6 = (float(omega[i]) for i in (7, 8, 10, 17, 23, 26))
+    c2, c4, c6 = CS2, CS2 ** 2, CS2 ** 3
 
     def collide(x):
-        r, j, p, q, s, w = x
-        a, b = p - CS2 * r, q - CS2 * r
+        r, j, p, q, s, w, v, t, z = x
+        a, b = p - c2 * r, q - c2 * r
         bulk, dev = (1 - wb) * (a + 2 * b), (1 - ws) * (a - b)
         at, bt = (bulk + 2 * dev) / 3, (bulk - dev) / 3
-        d = w - CS2 * CS2 * r
-        att = 0.0 if mcm else CS2 * (at + bt)
-        return np.array([r, j, CS2 * r + at, CS2 * r + bt, (1 - r3) * (s - CS2 * j) + CS2 * j,
-                         CS2 * CS2 * r + d + r4 * (att - d)], dtype=complex)
+        k120 = (1 - r3) * (s - c2 * j)
+        d, e = w - c4 * r, v - c4 * r
+        dt = d + r4 * ((0.0 if mcm else c2 * (at + bt)) - d)
+        et = e + r4 * ((0.0 if mcm else 2 * c2 * bt) - e)
+        k122 = t - c4 * j
+        k122 = k122 + r5 * ((0.0 if mcm else 0.8 * c2 * k120) - k122)
+        g = z - c6 * r
+        g = g + r6 * ((0.0 if mcm else (c4 * (at + 2 * bt) + c2 * (et + 2 * dt)) / 3) - g)
+        return np.array([r, j, c2 * r + at, c2 * r + bt, k120 + c2 * j, c4 * r + dt, c4 * r + et,
+                         k122 + c4 * j, c6 * r + g], dtype=complex)
 
     def stream(x):
         ph = {e: np.exp(-1j * k * e) for e in (-1, 0, 1)}
         out = []
-        for m0, m1, m2 in ((x[0], x[1], x[2]), (x[3], x[4], x[5])):
+        for m0, m1, m2 in ((x[0], x[1], x[2]), (x[3], x[4], x[5]), (x[6], x[7], x[8])):
             a = {0: ph[0] * (m0 - m2), 1: ph[1] * (m2 + m1) / 2, -1: ph[-1] * (m2 - m1) / 2}
             out += [a[0] + a[1] + a[-1], a[1] - a[-1], a[1] + a[-1]]
         return np.array(out)
 
-    eye = np.eye(6)
-    C = np.stack([collide(eye[i]) for i in range(6)], axis=1)
-    S = np.stack([stream(eye[i]) for i in range(6)], axis=1)
+    eye = np.eye(9)
+    C = np.stack([collide(eye[i]) for i in range(9)], axis=1)
+    S = np.stack([stream(eye[i]) for i in range(9)], axis=1)
     return S @ C
+
+
+# (e_x, e_y, e_z) exponents of the nine moments of sound_wave_step_matrix_3d, in its state order
+SOUND_WAVE_MOMENTS_3D = [(a, b, c) for (b, c) in ((0, 0), (2, 0), (2, 2)) for a in (0, 1, 2)]
