@@ -657,3 +657,33 @@ def test_poiseuille_profile_with_bounce_back():
     err = np.linalg.norm(u[0, :, 0] - prof) / np.linalg.norm(prof)
     assert err < 0.01
     assert np.max(np.abs(v)) < 1e-12
+
+
+@pytest.mark.parametrize("tau,drift", [(0.6, 0.0), (0.875, 0.0), (1.0, 0.0), (1.3, 0.0), (0.8, 0.3), (1.0, 0.25)])
+def test_poiseuille_is_exact_parabola_with_uniform_offset(tau, drift):
+    """Steady body-force channel between half-way bounce-back walls, solved exactly for the discrete
+    scheme: the x-odd moments j, m_110, m_120 of a flow u_x(y) obey, in steady state,
+    m~_120 = c_s^2 j + (3 - 2/r3) c_s^2 F (collision with the third-order source
+    (1 - r3/2) F kappa_020 of Eq. cmupdatesourceD3Q27 and the half-force velocity of Step 7, r3 the
+    third-order rate), and then j is exactly the parabola of nu = c_s^2 (tau - 1/2) in the bulk.
+    The bounce-back of the wall rows fixes its constant: u(y) = F/(2 nu)(y + 1/2)(ny - 1/2 - y) + du
+    with the uniform du = (16 Lambda - 3) F / (24 nu), Lambda = (tau - 1/2)(1/r3 - 1/2).  (This is
+    the two-relaxation-time result: exact walls at Lambda = 3/16, here tau = 7/8 with r3 = 1.)
+    Checked to 2e-6 F on every row; a missing third-order source or a velocity without the half
+    force changes du by O(F)."""
+    ny, Fx = 12, 1e-6
+    nu = CS2 * (tau - 0.5)
+    om = O.rates(tau, drift)
+    r3 = float(om[10])
+    lam = (tau - 0.5) * (1 / r3 - 0.5)
+    prof = W.poiseuille_profile(ny, Fx, nu)
+    shape = (1, ny, 1)
+    ux = np.broadcast_to(prof[None, :, None], shape).copy()
+    zero = np.zeros(shape)
+    f = O.init_equilibrium(np.ones(shape), ux, zero, zero)
+    steps = int(40 / (nu * (math.pi / ny) ** 2))  # 40 e-folds of the slowest mode
+    f = O.run(f, steps, bc=1, F=(Fx, 0, 0), omega=om)
+    _, u, v, _ = O.moments(f, (Fx, 0, 0))
+    du = (16 * lam - 3) * Fx / (24 * nu)
+    assert np.max(np.abs(u[0, :, 0] - prof - du)) < 2e-6 * Fx
+    assert np.max(np.abs(v)) < 1e-12
