@@ -59,3 +59,21 @@ def test_reference_arm_two_ranks_prints_once():
     assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
     assert d["n_gpus"] == 2 and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+    # same metric, unit, direction and workload name as the CUDA arm
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    tau = 3 * W.tgv_viscosity(16, 0.05, 1600.0) + 0.5
+    assert d["metric"] == bench.METRIC and d["higher_is_better"] is True
+    assert d["config"]["workload"] == bench.tgv_workload(16, tau)
+    for key in ("steps", "warmup", "ms_per_step", "scaling", "vs_baseline", "dtype", "data"):
+        assert key in d
+
+
+def test_reference_arm_other_workload_says_unavailable():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "channel", "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert d["impl"] == "reference" and "TGV" in d["unavailable"]
