@@ -180,8 +180,9 @@ def fpclbm_set_params(h, tau: float, drift: float = 0.0, diffusion: int = FPCLBM
 
 
 def fpclbm_set_rates(h, omega):
-    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
-    assert om.size == 27
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64)).reshape(-1)
+    if om.size != 27:
+        raise ValueError("omega needs 27 rates, got %d" % om.size)
     return _check(h, load().fpclbm_set_rates(h, om.ctypes.data_as(_D)))
 
 
@@ -356,8 +357,16 @@ class Lattice:
     def _f64(a):
         return np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
 
+    @classmethod
+    def _sized(cls, a, n, what):
+        """float64, flat and exactly n values: the library reads n values behind the pointer."""
+        a = cls._f64(a)
+        if a.size != n:
+            raise ValueError("%s: expected %d values, got %d" % (what, n, a.size))
+        return a
+
     def init_fields(self, rho, ux, uy, uz):
-        arrs = [self._f64(a) for a in (rho, ux, uy, uz)]
+        arrs = [self._sized(a, self.ncells, q) for a, q in zip((rho, ux, uy, uz), ("rho", "ux", "uy", "uz"))]
         return fpclbm_init_fields(self.h, *arrs, on_device=0)
 
     def set_params(self, tau, drift=0.0, diffusion=FPCLBM_DIFF_FP):
@@ -394,7 +403,7 @@ class Lattice:
         return f.reshape((27,) + self.shape) if self.shape is not None else f
 
     def set_populations(self, f):
-        return fpclbm_set_populations(self.h, self._f64(f))
+        return fpclbm_set_populations(self.h, self._sized(f, 27 * self.ncells, "populations"))
 
     def populations_at(self, cells):
         return fpclbm_get_populations_at(self.h, cells)
@@ -433,8 +442,9 @@ def fpclbm2d_set_params(h, tau: float, bulk_rate: float = 0.0, drift: float = 0.
 
 
 def fpclbm2d_set_rates(h, omega):
-    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
-    assert om.size == 9
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64)).reshape(-1)
+    if om.size != 9:
+        raise ValueError("omega needs 9 rates, got %d" % om.size)
     return _check2(h, load().fpclbm2d_set_rates(h, om.ctypes.data_as(_D)))
 
 
@@ -501,8 +511,17 @@ class Lattice2D:
     def _f64(a):
         return np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
 
+    @classmethod
+    def _sized(cls, a, n, what):
+        """float64, flat and exactly n values: the library reads n values behind the pointer."""
+        a = cls._f64(a)
+        if a.size != n:
+            raise ValueError("%s: expected %d values, got %d" % (what, n, a.size))
+        return a
+
     def init_fields(self, rho, ux, uy):
-        return fpclbm2d_init_fields(self.h, *(self._f64(a) for a in (rho, ux, uy)))
+        return fpclbm2d_init_fields(self.h, *(self._sized(a, self.ncells, q) for a, q in
+                                              zip((rho, ux, uy), ("rho", "ux", "uy"))))
 
     def set_params(self, tau, bulk_rate=0.0, drift=0.0, diffusion=FPCLBM_DIFF_FP):
         return fpclbm2d_set_params(self.h, tau, bulk_rate, drift, diffusion)
@@ -530,4 +549,4 @@ class Lattice2D:
         return f.reshape((9,) + self.shape)
 
     def set_populations(self, f):
-        return fpclbm2d_set_populations(self.h, self._f64(f))
+        return fpclbm2d_set_populations(self.h, self._sized(f, 9 * self.ncells, "populations"))

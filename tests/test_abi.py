@@ -70,3 +70,27 @@ def test_missing_library_raises(tmp_path):
             F.load(str(tmp_path / "nope.so"))
     finally:
         F._lib = saved
+
+
+def test_wrappers_reject_wrongly_sized_arrays_before_calling_the_library():
+    """The C ABI cannot see the length of a host buffer; the Python wrappers check it, so a wrong
+    size raises instead of letting the library read past the end of the array."""
+    import numpy as np
+    from paper_2410_09739_gb300 import fpclbm as F
+    lat = F.Lattice.__new__(F.Lattice)  # no device handle: every check must fire before the call
+    lat.ncells, lat.shape, lat.h = 4 * 3 * 2, (2, 3, 4), None
+    good = np.ones((2, 3, 4))
+    with pytest.raises(ValueError, match="uy"):
+        lat.init_fields(good, good, np.ones(5), good)
+    with pytest.raises(ValueError, match="populations"):
+        lat.set_populations(np.ones((27, 23)))
+    lat2 = F.Lattice2D.__new__(F.Lattice2D)
+    lat2.ncells, lat2.shape, lat2.h = 12, (3, 4), None
+    with pytest.raises(ValueError, match="rho"):
+        lat2.init_fields(np.ones(11), np.ones(12), np.ones(12))
+    with pytest.raises(ValueError, match="populations"):
+        lat2.set_populations(np.ones((9, 13)))
+    with pytest.raises(ValueError, match="27 rates"):
+        F.fpclbm_set_rates(None, np.ones(26))
+    with pytest.raises(ValueError, match="9 rates"):
+        F.fpclbm2d_set_rates(None, np.ones(10))
