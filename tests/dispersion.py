@@ -147,3 +147,55 @@ def sound_wave_step_matrix_3d(n, omega, mcm=False):
 
 # (e_x, e_y, e_z) exponents of the nine moments of sound_wave_step_matrix_3d, in its state order
 SOUND_WAVE_MOMENTS_3D = [(a, b, c) for (b, c) in ((0, 0), (2, 0), (2, 2)) for a in (0, 1, 2)]
+
+
+def crossing_shear_wave_step_matrix(kx, kz, omega, mcm=False):
+    """Linearised D3Q27 step of a small flow u_y(x, z) (no variation along y, rho = 1), for the
+    Fourier mode exp(i (kx x + kz z)); the crossing shear waves u_y = U cos(k x) cos(k z) of the
+    hyperviscosity study (Sec. 4) are four such modes with the same matrix up to mirror symmetry.
+
+    Weight the populations by e_y and sum over e_y: the nine raw moments m_a1c (a, c in 0..2) of
+    that y-odd part evolve on their own.  Collision, to first order around rest (u_y = m_010), with
+    central kappa_a1c = m_a1c - u_y m_a0c and the rest values m_000 = 1, m_200 = m_002 = c_s^2,
+    m_202 = c_s^4:
+      * kappa_110, kappa_011 relax at the shear rate omega_4 = omega_6 toward 0;
+      * kappa_210, kappa_012, kappa_111 relax at the third-order rate toward 0;
+      * kappa_211, kappa_112 relax at the fourth-order rate toward kappa~_200 kappa~_011 / rho and
+        kappa~_002 kappa~_110 / rho, linearised c_s^2 kappa~_011 and c_s^2 kappa~_110 (FP diffusion
+        tensor, post-collision second moments), 0 for the Maxwellian (MCM) attractors;
+      * kappa_212 relaxes at the fifth-order rate toward
+        (2 / 5 rho)(kappa~_200 kappa~_012 + kappa~_002 kappa~_210), linearised
+        (2/5) c_s^2 (kappa~_012 + kappa~_210), 0 for MCM;
+    and back with m_a1c = kappa~_a1c + u_y m_a0c.  Streaming moves the (e_x, e_z) populations of the
+    y-odd part by (e_x, e_z): a factor exp(-i (kx e_x + kz e_z)).  The fourth-order attractors are
+    where FP and MCM differ for this flow: with the Maxwellian ones the wave loses amplitude far
+    faster than exp(-nu (kx^2 + kz^2) t), the hyperviscosity the paper reports for MCM.  Returns
+    the complex 9x9 matrix of one step on the state m_a1c flattened as [a][c]."""
+    c2, c4 = CS2, CS2 * CS2
+    w, r3, r4, r5 = (float(omega[i]) for i in (4, 10, 17, 23))
+
+    def collide(m):
+        m = m.reshape(3, 3)
+        u = m[0, 0]
+        t110, t011 = (1 - w) * m[1, 0], (1 - w) * m[0, 1]
+        t210, t012, t111 = (1 - r3) * (m[2, 0] - c2 * u), (1 - r3) * (m[0, 2] - c2 * u), (1 - r3) * m[1, 1]
+        t211 = m[2, 1] + r4 * ((0.0 if mcm else c2 * t011) - m[2, 1])
+        t112 = m[1, 2] + r4 * ((0.0 if mcm else c2 * t110) - m[1, 2])
+        k212 = m[2, 2] - c4 * u
+        t212 = k212 + r5 * ((0.0 if mcm else 0.4 * c2 * (t012 + t210)) - k212)
+        return np.array([[u, t011, t012 + c2 * u], [t110, t111, t112], [t210 + c2 * u, t211, t212 + c4 * u]],
+                        dtype=complex).reshape(-1)
+
+    es = (0, 1, -1)
+    to_values = np.array([[1, 0, -1], [0, 0.5, 0.5], [0, -0.5, 0.5]])  # e = 0, +1, -1 from (m0, m1, m2)
+    to_moments = np.array([[1, 1, 1], [0, 1, -1], [0, 1, 1]])         # (m0, m1, m2) from e = 0, +1, -1
+    shift = np.array([[np.exp(-1j * (kx * ex + kz * ez)) for ez in es] for ex in es])
+
+    def stream(m):
+        h = to_values @ m.reshape(3, 3) @ to_values.T
+        return (to_moments @ (h * shift) @ to_moments.T).reshape(-1)
+
+    eye = np.eye(9)
+    C = np.stack([collide(eye[i]) for i in range(9)], axis=1)
+    S = np.stack([stream(eye[i].astype(complex)) for i in range(9)], axis=1)
+    return S @ C
