@@ -94,3 +94,35 @@ def test_wrappers_reject_wrongly_sized_arrays_before_calling_the_library():
         F.fpclbm_set_rates(None, np.ones(26))
     with pytest.raises(ValueError, match="9 rates"):
         F.fpclbm2d_set_rates(None, np.ones(10))
+
+
+def test_other_entry_points_reject_bad_arguments_before_touching_the_device(lib):
+    """Argument checks of the ensemble, D2Q9 and no-allocation entry points run on the host before
+    any CUDA call, so they can be exercised without a GPU."""
+    P = ctypes.c_void_p
+    h = P()
+    lib.fpclbm_create_ensemble.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int, P]
+    dims = (ctypes.c_int * 6)(8, 8, 8, 4, 0, 4)
+    tau = (ctypes.c_double * 2)(0.6, 0.6)
+    assert lib.fpclbm_create_ensemble(ctypes.byref(h), 0, dims, tau, 1, None) == -1       # no boxes
+    assert lib.fpclbm_create_ensemble(ctypes.byref(h), 1, dims, tau, 0, None) == -1       # FP32 only
+    assert lib.fpclbm_create_ensemble(ctypes.byref(h), 2, dims, tau, 1, None) == -1       # a side of 0
+    bad_tau = (ctypes.c_double * 1)(0.4)                                                   # 1/tau = 2.5
+    assert lib.fpclbm_create_ensemble(ctypes.byref(h), 1, dims, bad_tau, 1, None) == -4
+    assert h.value is None
+    lib.fpclbm2d_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    assert lib.fpclbm2d_create(ctypes.byref(h), 0, 8, 1, None) == -1
+    assert lib.fpclbm2d_create(ctypes.byref(h), 8, 8, 7, None) == -1
+    assert lib.fpclbm2d_create(ctypes.byref(h), 65536, 65536, 1, None) == -1
+    assert h.value is None
+    lib.fpclbm_diagnostics_noalloc.argtypes = [P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, P, P]
+    dummy = P(256)  # never dereferenced: every call below fails its checks first
+    assert lib.fpclbm_diagnostics_noalloc(None, 8, 0.0, 0.0, 0.0, dummy, None) == -1
+    assert lib.fpclbm_diagnostics_noalloc(dummy, 0, 0.0, 0.0, 0.0, dummy, None) == -1
+    assert lib.fpclbm_diagnostics_noalloc(dummy, 2 ** 31, 0.0, 0.0, 0.0, dummy, None) == -1
+    assert lib.fpclbm_diagnostics_noalloc(dummy, 8, float("inf"), 0.0, 0.0, dummy, None) == -1
+    lib.fpclbm_last_error.restype = ctypes.c_char_p
+    lib.fpclbm_last_error.argtypes = [P]
+    assert b"finite" in lib.fpclbm_last_error(None)
