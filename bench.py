@@ -42,6 +42,8 @@ import workloads as W  # noqa: E402
 
 METRIC = "D3Q27 FPC-LBM MLUPS & % HBM roofline; closure speedup at stated error"
 BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+# the GB300's nominal HBM3e bandwidth (~8 TB/s), beside the measured copy bandwidth of MEASURED_PEAKS.json
+NOMINAL_HBM_GBS = 8000.0
 
 
 def parse():
@@ -54,8 +56,11 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=list(BYTES))
     p.add_argument("--inner", type=int, default=64, help="LBM steps per bench step")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--variants", action="store_true", help="also time fp16/bf16 storage")
-    p.add_argument("--workload", default="tgv", choices=["tgv", "channel", "cavity", "ensemble", "shear2d"])
+    p.add_argument("--drift", type=float, default=0.0,
+                   help="omega_FP of the headline line: rates k * drift for orders k >= 3 (0: unit rates)")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the secondary entries (fp16/bf16 storage, general rates)")
+    p.add_argument("--workload", default="tgv", choices=["tgv", "channel", "cavity", "ensemble", "shear2d", "closure"])
     return p.parse_args()
 
 
@@ -291,6 +296,10 @@ def kernel_name(F, workload, launch):
         return "fpc::k_step2d (D2Q9, AA even/odd)"
     ens = workload == "ensemble"
     v = launch["variant"]
+    if v == 3:
+        return ("fpc::k_step_stage (AA even/odd; whole slot rows through %d shared-memory stages by bulk "
+                "asynchronous copies, two cells per thread, blocks of %d; collision mode %d: %s)"
+                % (launch["minb"], launch["block"], launch["mode"], F.LAUNCH_MODES.get(launch["mode"], "?")))
     if v == 2:
         base = "fpc::k_ens_pair" if ens else "fpc::k_step_pair"
         shape = "two cells per thread, blocks of 128"
@@ -318,15 +327,29 @@ def time_ours(lat, F, torch, args, n, steps, warmup, inner):
     return e0.elapsed_time(e1) / 1e3
 
 
-def setup(args, F, prec, stream):
-    """Build the lattice of the chosen workload; returns (lat, flat fields, cells, config dict)."""
+def closure_weights(seed):
+    """Seeded random closure weights (4865, layer shapes 9-64-64-1, scaled by 1/sqrt(fan-in)) as
+    bf16 bit patterns (round to nearest even)."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, 1 / 3.0, 64 * 9), np.zeros(64), rng.normal(0, 1 / 8.0, 64 * 64), np.zeros(64),
+             rng.normal(0, 1 / 8.0 * 0.01, 64), np.zeros(1)]
+    a = np.concatenate(parts).astype(np.float32).view(np.uint32).astype(np.uint64)
+    return ((a + ((a >> 16) & 1) + 0x7FFF) >> 16).astype(np.uint16)
+
+
+def setup(args, F, prec, stream, drift=0.0, learned=True):
+    """Build the lattice of the chosen workload; returns (lat, flat fields, cells, config dict).
+    drift > 0 selects the rates k * drift of orders k >= 3 (TGV only); learned=False runs the
+    closure workload's coarse channel without the closure."""
     if args.workload == "tgv":
         n, u0 = args.size, 0.05
         tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
         lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_PERIODIC, stream=stream)
-        lat.set_params(tau)
+        lat.set_params(tau, drift)
         flds = W.tgv(n, u0)
         cfg = {"workload": tgv_workload(n, tau)}
+        if drift > 0:
+            cfg["drift"] = drift
     elif args.workload == "channel":
         nx, ny, nz, u_star = 384, 192, 192, 0.005
         H = ny / 2
@@ -345,6 +368,24 @@ def setup(args, F, prec, stream):
         one = np.ones((n, n, n))
         flds = (one, 0 * one, 0 * one, 0 * one)
         cfg = {"workload": "lid-driven cubic cavity 150^3, Re=1000, Ma=0.1, walls on all faces, tau=%.6f" % tau}
+    elif args.workload == "closure":
+        # the learned closure's coarse channel: 192 x 96 x 96, Re_tau = 395 (H = 48, u* = 0.005), BF16
+        # storage by default; the headline leg runs the learned mode with seeded random bf16 weights
+        # (the inference cost does not depend on their values), the secondary leg plain FPC-LBM
+        nx, ny, nz, u_star = 192, 96, 96, 0.005
+        H = ny / 2
+        tau = 3 * (u_star * H / 395.0) + 0.5
+        lat = F.Lattice(nx, ny, nz, prec, F.FPCLBM_BC_WALLS_Y, stream=stream)
+        if learned:
+            lat.set_closure(closure_weights(seed=11))
+            lat.set_params(tau, 0.0, F.FPCLBM_DIFF_FP_LEARNED)
+        else:
+            lat.set_params(tau)
+        lat.set_force(u_star ** 2 / H, 0.0, 0.0)
+        flds = W.channel_fields(nx, ny, nz, u_star, seed=7)
+        cfg = {"workload": "learned-closure coarse channel Re_tau=395 192x96x96, y walls, body force, tau=%.6f, "
+                           "%s" % (tau, "FP + learned closure (MLP 9-64-64-1, random bf16 weights)" if learned
+                                   else "plain FP")}
     elif args.workload == "shear2d":
         n, U = 4096, 0.2 / 3 ** 0.5
         tau = 0.5 + 3 * U * n / 30000.0
@@ -378,25 +419,35 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream().cuda_stream
     prec0 = args.precision if args.workload != "ensemble" else "fp32"
+    if args.workload == "closure" and args.precision == "fp32" and "--precision" not in sys.argv:
+        prec0 = "bf16"  # the closure study's storage
     two_d = args.workload == "shear2d"
     qb = 18 if two_d else 54  # algorithmic bytes per cell update in units of the storage size
     results = {}
-    precs = [prec0] + ([p for p in ("fp16", "bf16") if p != prec0] if args.variants and args.workload != "ensemble"
-                       else [])
+    # legs: the headline line first, then the secondary entries (same workload; 16-bit deviation
+    # storage and, for the TGV, the general-rate kernel with omega_k = k * drift for k >= 3)
+    legs = [("headline", prec0, args.drift, True)]
+    if args.workload == "closure":
+        legs.append(("plain_coarse", prec0, 0.0, False))
+    elif not args.no_variants and args.workload != "ensemble":
+        legs += [(p, p, args.drift, True) for p in ("fp16", "bf16") if p != prec0]
+        if args.workload == "tgv" and args.drift == 0.0:
+            legs.append(("fp32_general_rates", "fp32", 0.3, True))
     cfg = None
-    for prec in precs:
-        lat, flat, ncell, c = setup(args, F, prec, stream)
+    for key, prec, drift, learned in legs:
+        lat, flat, ncell, c = setup(args, F, prec, stream, drift, learned)
         if cfg is None:
             cfg = c
         barrier(world)
-        clocks = Clocks(local) if (rank == 0 and prec == prec0) else None
+        clocks = Clocks(local) if rank == 0 else None
         if clocks:
             clocks.start()
         el = time_ours(lat, F, torch, args, ncell, args.steps, args.warmup, args.inner)
         ck = clocks.stop() if clocks else None
         el = max_over_ranks(el, world)
-        results[prec] = {"seconds": el, "clocks": ck, "launch": lat.launch() if not two_d else None}
-        if prec == prec0:
+        results[key] = {"seconds": el, "clocks": ck, "launch": lat.launch() if not two_d else None,
+                        "prec": prec, "drift": drift}
+        if key == "headline":
             # e2e: host buffers through the C ABI, copies inside the timed region
             nf = 3 if two_d else 4
             hb = [torch.empty(ncell, dtype=torch.float64).pin_memory().numpy() for _ in range(2 * nf)]
@@ -414,12 +465,12 @@ def main():
                 init(lat.h, *hb[:nf], on_device=0)
                 lat.step(args.inner)
                 mom(lat.h, *hb[nf:], on_device=0)
-            results[prec]["e2e_s"] = max_over_ranks(time.perf_counter() - t0, world)
+            results[key]["e2e_s"] = max_over_ranks(time.perf_counter() - t0, world)
         lat.close()
     if rank != 0:
         return
     prec = prec0
-    el = results[prec]["seconds"]
+    el = results["headline"]["seconds"]
     value = ncell * args.inner * args.steps * world / el / 1e6
     launches = args.inner * args.steps
     per_launch = el / launches
@@ -429,26 +480,37 @@ def main():
     cfg.update({"precision": prec, "storage": prec, "lbm_steps_per_bench_step": args.inner,
                 "l2": "inputs larger than L2 (%.2f GB populations)" % (27 * BYTES[prec] * ncell / 1e9),
                 "parallelism": "replicas" if world > 1 else "1 GPU"})
-    kname = kernel_name(F, args.workload, results[prec]["launch"])
+    kname = kernel_name(F, args.workload, results["headline"]["launch"])
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
+                     "frac": achieved / peak, "peak_nominal": NOMINAL_HBM_GBS,
+                     "frac_nominal": achieved / NOMINAL_HBM_GBS,
                      "traffic": ncu_traffic(prec, args.size) if args.workload == "tgv" else None,
                      "peak_source": peak_kind, "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes},
-        "e2e": {"value": ncell * args.inner * args.steps * world / results[prec]["e2e_s"] / 1e6, "unit": "MLUPS",
+        "e2e": {"value": ncell * args.inner * args.steps * world / results["headline"]["e2e_s"] / 1e6,
+                "unit": "MLUPS",
                 "h2d_bytes_per_step": (3 if two_d else 4) * 8 * ncell,
                 "d2h_bytes_per_step": (3 if two_d else 4) * 8 * ncell},
         "gpu_launches": launches,
-        "clocks": results[prec]["clocks"],
+        "clocks": results["headline"]["clocks"],
     }
+    if args.drift > 0:
+        cfg["drift"] = args.drift
     if len(results) > 1:
-        out["variants"] = {p: {"MLUPS": ncell * args.inner * args.steps * world / r["seconds"] / 1e6,
-                               "frac_hbm": qb * BYTES[p] * ncell / (r["seconds"] / launches) / 1e9 / peak}
-                           for p, r in results.items()}
+        out["variants"] = {}
+        for key, r in results.items():
+            if key == "headline":
+                continue
+            ach = qb * BYTES[r["prec"]] * ncell / (r["seconds"] / launches) / 1e9
+            out["variants"][key] = {
+                "storage": r["prec"], "drift": r["drift"], "MLUPS": ncell * launches * world / r["seconds"] / 1e6,
+                "ms_per_step": r["seconds"] / args.steps * 1e3, "achieved_gbs": ach, "frac": ach / peak,
+                "frac_nominal": ach / NOMINAL_HBM_GBS, "clocks": r["clocks"],
+                "kernel": kernel_name(F, args.workload, r["launch"])}
     if world == 1 and not args.no_cpu_baseline:
         if two_d:
             U = 0.2 / 3 ** 0.5

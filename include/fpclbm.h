@@ -167,8 +167,10 @@ FPCLBM_API int fpclbm_set_wall_velocity(fpclbm_t h, double ux, double uz);
 /* Advance n >= 0 time steps (collide + stream each).  Replays a captured CUDA
  * graph of the step loop; synchronises the stream once at the end and reads
  * the divergence flag: DIVERGED if any cell saw rho <= 0, NaN or Inf (the
- * populations are then whatever the last step wrote).  Errors: ARG, STATE,
- * CUDA, DIVERGED. */
+ * populations are then whatever the last step wrote); TIMEOUT if a step
+ * kernel's bounded wait for data it staged in shared memory ran out (about a
+ * second; that block stored nothing, so the state is not a valid step).
+ * Errors: ARG, STATE, CUDA, DIVERGED, TIMEOUT. */
 FPCLBM_API int fpclbm_step(fpclbm_t h, long long n);
 
 /* Density and half-force velocity of every cell (Appendix D Step 7:
@@ -195,7 +197,8 @@ FPCLBM_API int fpclbm_diagnostics(fpclbm_t h, double out[5]);
  *           f[alpha * ncells + cell] in the paper's alpha order (the layout of
  *           fpclbm_get_populations);
  *   ncells  1 .. FPCLBM_NOALLOC_MAX_CELLS, else ARG;
- *   Fx..Fz  body force, for the half-force velocity of Step 7;
+ *   Fx..Fz  body force; the velocity includes half of it, as in
+ *           fpclbm_diagnostics;
  *   out     device pointer to 5 doubles: sum rho, sum rho u (3), sum rho|u|^2/2;
  *   cuda_stream  stream to run on (NULL = legacy default stream); the call
  *           does not synchronise it.
@@ -203,6 +206,9 @@ FPCLBM_API int fpclbm_diagnostics(fpclbm_t h, double out[5]);
  * on every device that loads it, kept until the process exits).  The first
  * call on a device looks up that array's device address with the device
  * current and caches it: make that first call before any stream capture.
+ * The cached address belongs to the device's current primary context: do not
+ * use this entry point across a cudaDeviceReset (or anything else that
+ * destroys that context) in the same process.
  * Calls share the array; each overwrites the partials it reads, so nothing
  * needs clearing, but calls that overlap on the GPU race -- order them on one
  * stream.  Errors: ARG, CUDA (text via fpclbm_last_error(NULL)). */
@@ -223,20 +229,59 @@ FPCLBM_API int fpclbm_set_populations(fpclbm_t h, const double* f);
  * STATE, CUDA. */
 FPCLBM_API int fpclbm_get_populations_at(fpclbm_t h, const long long* cells, int n, double* f);
 
-/* Steps taken since the last init_fields / set_populations. */
+/* Steps taken since the last init_fields / set_populations (or the count
+ * given to set_state). */
 FPCLBM_API int fpclbm_get_step_count(fpclbm_t h, long long* steps);
+
+/* Raw state for bit-identical checkpoint and resume (no counterpart in the
+ * paper, which runs no restarts).  get/set_populations go through full fp64
+ * populations, which can move the last bit of a stored fp32 or 16-bit
+ * deviation; these move the stored deviations themselves, in the storage type
+ * and in the library's own layout: for each box in order, 27 slot rows of
+ * stride entries (slot s = (ex+1) + 3 (ey+1) + 9 (ez+1), cell x + nx (y + ny z),
+ * stride = the box's cell count rounded up to a multiple of 64, the padding
+ * entries included), each entry the deviation f - w of the rest state.  Which
+ * slot holds which population depends on the AA pattern's parity, i.e. on the
+ * step count, which travels with the state.
+ *   fpclbm_state_bytes  *bytes = the size of the raw state.
+ *   fpclbm_get_state    copies it to raw (host memory of exactly that many
+ *                       bytes) and the step count to *steps.  Errors: ARG
+ *                       (NULL pointer, wrong size), STATE (before init), CUDA.
+ *   fpclbm_set_state    replaces the populations by raw and the step count by
+ *                       steps >= 0; the handle is then initialised.  The state
+ *                       must come from a handle of the same dimensions,
+ *                       precision and boundary kind.  Errors: ARG, CUDA.
+ * A resumed run repeats the uninterrupted run bit for bit when the same
+ * parameters are set and the same kernel variant runs (the autotuner's choice
+ * is cached per process; FPCLBM_TUNE_CACHE or FPCLBM_LAUNCH pin it across
+ * processes). */
+FPCLBM_API int fpclbm_state_bytes(fpclbm_t h, unsigned long long* bytes);
+FPCLBM_API int fpclbm_get_state(fpclbm_t h, void* raw, unsigned long long bytes, long long* steps);
+FPCLBM_API int fpclbm_set_state(fpclbm_t h, const void* raw, unsigned long long bytes, long long steps);
+
+/* Test hook (no counterpart in the paper): every device and page-locked host
+ * allocation of the library's handles and training scratch goes through one
+ * wrapper that counts live allocations.  fail_after >= 0 makes the allocation
+ * that follows fail_after further successful ones fail as if the device were
+ * out of memory (once); -1 disarms; other values leave the setting as it is.
+ * *live (if not NULL) receives the number of live allocations, so a test can
+ * check that a failed call freed everything it had allocated.  Returns OK. */
+FPCLBM_API int fpclbm_test_alloc_hook(int fail_after, long long* live);
 
 /* Launch configuration of the step kernel, for reports (no counterpart in the
  * paper: it names which of the library's equivalent kernels runs).  Valid after
  * the first fpclbm_step since the last change of parameters, force or wall
  * velocity (the autotuner chooses then); before that FPCLBM_ERR_STATE.
  * out[0] threads per block; out[1] register-cap class (resident blocks of the
- * one-cell kernel: 1 none, 2 ~128, 3 ~80, 4 64 registers); out[2] variant
- * (0 one cell per thread, 1 cp.async-pipelined, 2 two cells per thread on the
- * packed fp32 pipe; ensembles: 0 or 2); out[3] collision mode (0 FP, 1 MCM,
- * 2 FP + learned closure, 3 FP + Smagorinsky, 4 FP and 5 MCM with every rate
- * of orders 3-6 equal to 1, where those moments are set to their attractors
- * plus half their body-force sources).  out is caller-owned int[4]. */
+ * one-cell kernel: 1 none, 2 ~128, 3 ~80, 4 64 registers), or for variant 3
+ * its number of shared-memory stages; out[2] variant (0 one cell per thread,
+ * 1 cp.async-pipelined, 2 two cells per thread on the packed fp32 pipe, 3 two
+ * cells per thread with whole slot rows moved through shared memory by bulk
+ * asynchronous copies; ensembles: 0 or 2); out[3] collision mode (0 FP, 1 MCM,
+ * 2 FP + learned closure, 3 FP + Smagorinsky, 4 FP, 5 MCM and 6 FP + learned
+ * closure with every rate of orders 3-6 equal to 1, where those moments are set
+ * to their attractors plus half their body-force sources).  out is
+ * caller-owned int[4]. */
 FPCLBM_API int fpclbm_get_launch(fpclbm_t h, int out[4]);
 
 /* Install the learned closure used by FPCLBM_DIFF_FP_LEARNED: a per-cell

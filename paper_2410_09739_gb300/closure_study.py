@@ -52,6 +52,9 @@ def parse(argv=None):
     p.add_argument("--precision", default="bf16")
     p.add_argument("--seed", type=int, default=7)
     p.add_argument("--cs", type=float, default=0.1, help="Smagorinsky constant of the non-learned baseline")
+    p.add_argument("--vortices", type=float, default=0.0,
+                   help="amplitude (units of u*) of large-scale streaks and streamwise vortices added to the "
+                        "fine run's initial state to trigger transition (0: laminar profile and noise only)")
     return p.parse_args(argv)
 
 
@@ -97,13 +100,19 @@ def run(args):
     out = {"config": {"fine": [nxf, nyf, nzf], "coarse": [nxc, nyc, nzc], "r": r, "re_tau": args.re_tau,
                       "u_star": us, "tau_fine": tau_f, "tau_coarse": tau_c, "F_fine": Ff, "F_coarse": Fc,
                       "friction_time_fine_steps": Tf, "precision": args.precision,
-                      "spinup_T": args.spinup, "collect_T": args.collect, "snap_T": args.snap}}
+                      "spinup_T": args.spinup, "collect_T": args.collect, "snap_T": args.snap,
+                      "vortices_over_u_star": args.vortices, "seed": args.seed}}
 
     # 1. fine spin-up
     fine = F.Lattice(nxf, nyf, nzf, args.precision, F.FPCLBM_BC_WALLS_Y, stream=stream)
     fine.set_params(tau_f)
     fine.set_force(Ff, 0.0, 0.0)
-    fine.init_fields(*W.channel_fields(nxf, nyf, nzf, us, seed=args.seed))
+    rho0, ux0, uy0, uz0 = W.channel_fields(nxf, nyf, nzf, us, seed=args.seed)
+    if args.vortices > 0:
+        from paper_2410_09739_gb300.channel_les_study import perturbation
+        du, dv, dw = perturbation(nxf, nyf, nzf, nyf, args.vortices * us, full=True)
+        ux0, uy0, uz0 = ux0 + du, uy0 + dv, uz0 + dw
+    fine.init_fields(rho0, ux0, uy0, uz0)
     n_spin = int(round(args.spinup * Tf))
     t0 = time.perf_counter()
     done = 0

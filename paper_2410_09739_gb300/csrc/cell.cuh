@@ -200,7 +200,7 @@ template <typename S, bool ODD, int BC, bool FORCE, int MODE>
 __device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom& G, unsigned c1, unsigned half,
                                             unsigned ncells, const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4,
                                             f2 om5, f2 om6, f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0),
-                                            f2 lid6z = f2(0.0))
+                                            f2 lid6z = f2(0.0), const float* closure = nullptr, bool active = true)
 {
     const unsigned stride = G.stride;
     f2 g[27];
@@ -214,7 +214,8 @@ __device__ __forceinline__ void update_pair(S* __restrict__ buf, const CellGeom&
 #pragma unroll
         for (int s = 0; s < 27; ++s) g[s].v.y = Store<S>::ld(load_ptr<S, ODD, BC>(buf, s, n, stride, c2));
     }
-    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
+    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, closure);
+    if (!active) return;  // a tail lane of the warp-collective learned mode: nothing to write
     if (!ok) atomicOr(flag, 1);
     asm volatile("" : "+r"(c1));  // rebuild the store addresses (see update_cell)
     lid_correct_pair<BC>(g, G, c1, c1 + half < ncells ? c1 + half : c1, lid6x, lid6z);
@@ -269,7 +270,8 @@ struct Store2<__nv_bfloat16> {
 template <typename S, int BC, bool FORCE, int MODE>
 __device__ __forceinline__ void update_pair_even(S* __restrict__ buf, const CellGeom& G, unsigned t, unsigned ncells,
                                                  const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5, f2 om6,
-                                                 f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0), f2 lid6z = f2(0.0))
+                                                 f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0), f2 lid6z = f2(0.0),
+                                                 const float* closure = nullptr, bool active = true)
 {
     const unsigned stride = G.stride;
     unsigned c = 2 * t;
@@ -285,7 +287,8 @@ __device__ __forceinline__ void update_pair_even(S* __restrict__ buf, const Cell
             g[s] = f2(v, v);
         }
     }
-    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
+    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, closure);
+    if (!active) return;
     if (!ok) atomicOr(flag, 1);
     asm volatile("" : "+r"(c));  // rebuild the store addresses (see update_cell)
     lid_correct_pair<BC>(g, G, c, two ? c + 1 : c, lid6x, lid6z);
@@ -313,7 +316,8 @@ template <typename S, int BC, bool FORCE, int MODE>
 __device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const CellGeom& G, unsigned t,
                                                     const Rates<f2>& rt, f2 Fx, f2 Fy, f2 Fz, f2 om4, f2 om5,
                                                     f2 om6, f2 om8, f2 om9, int* flag, f2 lid6x = f2(0.0),
-                                                    f2 lid6z = f2(0.0))
+                                                    f2 lid6z = f2(0.0), const float* closure = nullptr,
+                                                    bool active = true)
 {
     static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y || BC == BC_WALLS_Y_LID || BC == BC_BOX_LID,
                   "no symmetry plane");
@@ -345,7 +349,8 @@ __device__ __forceinline__ void update_pair_odd_adj(S* __restrict__ buf, const C
             }
         }
     }
-    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, nullptr);
+    const bool ok = collide_cell<f2, FORCE, MODE>(g, rt, Fx, Fy, Fz, om4, om5, om6, om8, om9, closure);
+    if (!active) return;
     if (!ok) atomicOr(flag, 1);
     asm volatile("" : "+r"(c));  // rebuild the store addresses (see update_cell)
     lid_correct_pair<BC>(g, G, c, c + 1, lid6x, lid6z);

@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "pair.cuh"
 
 namespace fpc {
 
@@ -126,6 +127,22 @@ __device__ R closure_delta_omega(const uint32_t* __restrict__ P, const R in[9])
         if ((lane >> 4) == (unsigned)mt) mine = r < 8 ? vlo : vhi;
     }
     return (R)(mine + __ldg(Pf + CP_B3));
+}
+
+// Two cells per thread (pair.cuh): the network runs once for the cells in the x lanes of the
+// warp and once for those in the y lanes (warp-collective, like the scalar version).
+template <>
+__device__ __forceinline__ f2 closure_delta_omega<f2>(const uint32_t* __restrict__ P, const f2 in[9])
+{
+    float ix[9], iy[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        ix[k] = in[k].v.x;
+        iy[k] = in[k].v.y;
+    }
+    const float dx = closure_delta_omega<float>(P, ix);
+    const float dy = closure_delta_omega<float>(P, iy);
+    return f2(dx, dy);
 }
 
 }  // namespace fpc

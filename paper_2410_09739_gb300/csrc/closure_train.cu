@@ -10,12 +10,14 @@
 //   weights in the forward and backward kernels, fp32 accumulation and
 //   gradients, fp64 loss accumulation, fp32 master weights.
 // fpclbm_closure_grad:   one loss/gradient evaluation, for checking.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include "rtalloc.h"
 #include "aux.cuh"
 #include "closure.cuh"
 #include "handle.h"
@@ -136,8 +138,26 @@ __global__ void k_cl_label(const double* __restrict__ acc, int cx, int cy, int c
 // Network forward/backward on mini-batches
 // ---------------------------------------------------------------------------
 
-constexpr int kB = 64;          // samples per block
-constexpr int kPad = kB + 1;    // padded row length of the per-sample tables
+// Mini-batch forward and backward on the tensor cores.  A block takes kMB = 128
+// samples, 32 per warp (two 16-row tiles).  Every contraction is an
+// mma.sync.m16n8k16 bf16 x bf16 -> fp32 product:
+//   forward   Z1 = [x, 1] [W1 | b1]^T (K = 16: 9 inputs, the bias input 1, zeros),
+//             Z2 = H1 W2^T (K = 64), H = tanh(Z) in fp32, y = w3 . H2 + b3 in fp32;
+//   backward  G2 = gy w3 (1 - H2^2), G1 = (G2 W2) (1 - H1^2)  (K = 64);
+//   weights   dW2 = G2^T [H1, 1] and dW1 = G1^T [x, 1] over the block's samples
+//             (K = 128); the column of ones gives the bias gradients db2, db1;
+//             dw3 = sum gy H2 and db3 = sum gy in fp32.
+// The operands x, H1, G2, G1 are rounded to bf16 (the weights are bf16 already);
+// products accumulate in fp32.  The fp32 accumulator fragments of one product
+// are the A-operand fragments of the next (row g / g+8, columns 2t, 2t+1), so
+// H1 and G2 stay in registers; for the weight gradients, whose K runs over the
+// samples, H1, G2, G1 and x are also written feature-major to shared memory.
+// Each block writes its gradient (4865 fp32) and its loss (fp64) to its own
+// slot of a scratch array; k_cl_reduce_adam / k_cl_reduce_grad sum the blocks
+// in a fixed order, so training is deterministic.
+
+constexpr int kMB = 128;        // samples per block (4 warps x 32)
+constexpr int kTP = kMB + 8;    // row pitch of the feature-major tables (bank offset between rows)
 
 struct NetArgs {
     const float* X;             // [n][9]
@@ -149,114 +169,275 @@ struct NetArgs {
     float mu[10], inv_sd[10];   // standardisation of the 9 inputs and the target
     float scale;                // dL/dy factor 2 / batch
     const __nv_bfloat16* W;     // bf16 weights (closure layout)
-    float* grad;                // fp32 gradient accumulator [4865]
-    double* loss;               // fp64 sum of squared errors
+    float* part;                // per-block gradients [blocks][4865]
+    double* part_loss;          // per-block sums of squared errors [blocks]
 };
 
-// dynamic shared memory: weights (4868 floats) then per-sample tables
-constexpr int kSmemFloats = 4868 + kPad * (9 + 64 * 4 + 1);
+struct TrainSmem {
+    __nv_bfloat16 W1p[64][16];  // [j][i]: W1, then b1 in column 9, zeros
+    __nv_bfloat16 W2s[64][64];  // W2[j][k]
+    __nv_bfloat16 W2T[64][64];  // W2[j][k] at [k][j]
+    __nv_bfloat16 XS[kMB][16];  // [m][i] inputs of the block's samples, 1 in column 9
+    __nv_bfloat16 XT[16][kTP];  // [i][m]
+    __nv_bfloat16 H1T[72][kTP]; // [k][m], row 64 = 1, rows 65..71 = 0
+    __nv_bfloat16 G2T[64][kTP]; // [j][m]
+    __nv_bfloat16 G1T[64][kTP]; // [j][m]
+    float b2[64], w3[64], tgt[kMB], vld[kMB], dw3[4][64];
+    float b3, db3[4];
+    double loss[4];
+};
 
-__global__ void __launch_bounds__(kB) k_cl_fwd_bwd(NetArgs a)
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ __nv_bfloat16 bf_lo(uint32_t v) { return __ushort_as_bfloat16((unsigned short)(v & 0xffffu)); }
+__device__ __forceinline__ __nv_bfloat16 bf_hi(uint32_t v) { return __ushort_as_bfloat16((unsigned short)(v >> 16)); }
+
+__global__ void __launch_bounds__(kMB) k_cl_mma(NetArgs a)
 {
-    extern __shared__ __align__(16) float sm[];
-    float* sW = sm;                     // closure layout
-    float* sX = sm + 4868;              // [9][kPad]
-    float* sH1 = sX + 9 * kPad;         // [64][kPad]
-    float* sH2 = sH1 + 64 * kPad;       // [64][kPad]
-    float* sG2 = sH2 + 64 * kPad;       // [64][kPad]  dL/da2
-    float* sG1 = sG2 + 64 * kPad;       // [64][kPad]  dL/da1
-    float* sGY = sG1 + 64 * kPad;       // [kPad]      dL/dy
-    __shared__ double sLoss[kB];
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(cl_smem);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
 
-    for (int i = threadIdx.x; i < CL_N; i += kB) sW[i] = __bfloat162float(a.W[i]);
-    __syncthreads();
-
-    const int tid = threadIdx.x;
-    const unsigned long long pos = a.first + (unsigned long long)blockIdx.x * kB + tid;
-    const bool valid = pos < a.first + a.count;
-    float x[9], t = 0.f;
-    if (valid) {
-        const unsigned long long idx = (a.perm_a * pos + a.perm_c) % a.n;
-        for (int i = 0; i < 9; ++i) x[i] = (a.X[idx * 9 + i] - a.mu[i]) * a.inv_sd[i];
-        t = (a.T[idx] - a.mu[9]) * a.inv_sd[9];
-    } else {
-        for (int i = 0; i < 9; ++i) x[i] = 0.f;
+    for (int i = tid; i < 64 * 16; i += kMB) {
+        const int j = i >> 4, c = i & 15;
+        S.W1p[j][c] = c < 9 ? a.W[CL_W1 + 9 * j + c] : (c == 9 ? a.W[CL_B1 + j] : zero);
     }
-    // layer 1 (h1 kept in registers with compile-time indices, and in shared memory)
-    float h1[64];
+    for (int i = tid; i < 4096; i += kMB) {
+        const __nv_bfloat16 v = a.W[CL_W2 + i];
+        S.W2s[i >> 6][i & 63] = v;
+        S.W2T[i & 63][i >> 6] = v;
+    }
+    for (int j = tid; j < 64; j += kMB) {
+        S.b2[j] = __bfloat162float(a.W[CL_B2 + j]);
+        S.w3[j] = __bfloat162float(a.W[CL_W3 + j]);
+    }
+    if (tid == 0) S.b3 = __bfloat162float(a.W[CL_B3]);
+    for (int i = tid; i < 8 * kTP; i += kMB) S.H1T[64 + i / kTP][i % kTP] = i < kTP ? one : zero;
+    // this thread's sample: standardised inputs (bf16), bias input 1, target
+    {
+        const unsigned long long pos = a.first + (unsigned long long)blockIdx.x * kMB + tid;
+        const bool valid = pos < a.first + a.count;
+        float x[16];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
-        float s = sW[CL_B1 + j];
+        for (int i = 0; i < 16; ++i) x[i] = 0.f;
+        x[9] = 1.f;
+        float tt = 0.f;
+        if (valid) {
+            const unsigned long long idx = (a.perm_a * pos + a.perm_c) % a.n;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s = fmaf(sW[CL_W1 + 9 * j + i], x[i], s);
-        h1[j] = tanhf(s);
-        sH1[j * kPad + tid] = h1[j];
-    }
-    for (int i = 0; i < 9; ++i) sX[i * kPad + tid] = x[i];
-    // layer 2 and output
-    float y = sW[CL_B3];
-    for (int j = 0; j < 64; ++j) {
-        float s = sW[CL_B2 + j];
-#pragma unroll
-        for (int k = 0; k < 64; ++k) s = fmaf(sW[CL_W2 + 64 * j + k], h1[k], s);
-        const float h = tanhf(s);
-        sH2[j * kPad + tid] = h;
-        y = fmaf(sW[CL_W3 + j], h, y);
-    }
-    const float err = valid ? (y - t) : 0.f;
-    const float gy = a.scale * err;
-    sLoss[tid] = (double)err * (double)err;
-    sGY[tid] = gy;
-    for (int j = 0; j < 64; ++j) {
-        const float h = sH2[j * kPad + tid];
-        sG2[j * kPad + tid] = gy * sW[CL_W3 + j] * (1.f - h * h);
-    }
-    // dL/dh1 = W2^T dL/da2, then through tanh
-    for (int k = 0; k < 64; ++k) {
-        float s = 0.f;
-#pragma unroll 8
-        for (int j = 0; j < 64; ++j) s = fmaf(sW[CL_W2 + 64 * j + k], sG2[j * kPad + tid], s);
-        const float h = sH1[k * kPad + tid];
-        sG1[k * kPad + tid] = s * (1.f - h * h);
-    }
-    __syncthreads();
-
-    // parameter gradients summed over the block's samples
-    for (int p = tid; p < CL_N; p += kB) {
-        float s = 0.f;
-        if (p < CL_B1) {  // W1[j][i]
-            const int j = p / 9, i = p % 9;
-            for (int m = 0; m < kB; ++m) s = fmaf(sG1[j * kPad + m], sX[i * kPad + m], s);
-        } else if (p < CL_W2) {  // b1[j]
-            const int j = p - CL_B1;
-            for (int m = 0; m < kB; ++m) s += sG1[j * kPad + m];
-        } else if (p < CL_B2) {  // W2[j][k]
-            const int j = (p - CL_W2) / 64, k = (p - CL_W2) % 64;
-            for (int m = 0; m < kB; ++m) s = fmaf(sG2[j * kPad + m], sH1[k * kPad + m], s);
-        } else if (p < CL_W3) {  // b2[j]
-            const int j = p - CL_B2;
-            for (int m = 0; m < kB; ++m) s += sG2[j * kPad + m];
-        } else if (p < CL_B3) {  // W3[j]
-            const int j = p - CL_W3;
-            for (int m = 0; m < kB; ++m) s = fmaf(sGY[m], sH2[j * kPad + m], s);
-        } else {  // b3
-            for (int m = 0; m < kB; ++m) s += sGY[m];
+            for (int i = 0; i < 9; ++i) x[i] = (a.X[idx * 9 + i] - a.mu[i]) * a.inv_sd[i];
+            tt = (a.T[idx] - a.mu[9]) * a.inv_sd[9];
         }
-        atomicAdd(a.grad + p, s);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(x[i]);
+            S.XS[tid][i] = b;
+            S.XT[i][tid] = b;
+        }
+        S.tgt[tid] = tt;
+        S.vld[tid] = valid ? 1.f : 0.f;  // padding rows of a short batch: no error, no gradient
     }
-    if (tid == 0) {
-        double l = 0;
-        for (int m = 0; m < kB; ++m) l += sLoss[m];
-        atomicAdd(a.loss, l);
+    __syncthreads();
+
+    float dw3a[8][2];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) dw3a[nt][0] = dw3a[nt][1] = 0.f;
+    float db3a = 0.f;
+    double lossa = 0.0;
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = 32 * w + 16 * mt + g, r1 = r0 + 8;
+        // ---- layer 1: Z1 = [x, 1] [W1 | b1]^T, H1 = tanh(Z1)
+        const uint32_t xa0 = lds32(&S.XS[r0][2 * t]), xa1 = lds32(&S.XS[r1][2 * t]);
+        const uint32_t xa2 = lds32(&S.XS[r0][2 * t + 8]), xa3 = lds32(&S.XS[r1][2 * t + 8]);
+        float h1[8][4];
+        uint32_t A2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16_16816(c, xa0, xa1, xa2, xa3, lds32(&S.W1p[8 * nt + g][2 * t]), lds32(&S.W1p[8 * nt + g][2 * t + 8]));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h1[nt][q] = tanhf(c[q]);
+            const uint32_t lo = pack_bf16x2(h1[nt][0], h1[nt][1]), hi = pack_bf16x2(h1[nt][2], h1[nt][3]);
+            A2[nt >> 1][(nt & 1) * 2] = lo;
+            A2[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            const int c0 = 8 * nt + 2 * t;
+            S.H1T[c0][r0] = bf_lo(lo);
+            S.H1T[c0 + 1][r0] = bf_hi(lo);
+            S.H1T[c0][r1] = bf_lo(hi);
+            S.H1T[c0 + 1][r1] = bf_hi(hi);
+            // the backward pass needs 1 - H1^2 of the bf16 operand's source value
+            h1[nt][0] = 1.f - h1[nt][0] * h1[nt][0];
+            h1[nt][1] = 1.f - h1[nt][1] * h1[nt][1];
+            h1[nt][2] = 1.f - h1[nt][2] * h1[nt][2];
+            h1[nt][3] = 1.f - h1[nt][3] * h1[nt][3];
+        }
+        // ---- layer 2 and output: Z2 = H1 W2^T + b2, H2 = tanh(Z2), y = w3 . H2 + b3
+        float h2[8][4];
+        float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt)
+                mma_bf16_16816(c, A2[kt][0], A2[kt][1], A2[kt][2], A2[kt][3], lds32(&S.W2s[8 * nt + g][16 * kt + 2 * t]),
+                               lds32(&S.W2s[8 * nt + g][16 * kt + 2 * t + 8]));
+            const int c0 = 8 * nt + 2 * t;
+            h2[nt][0] = tanhf(c[0] + S.b2[c0]);
+            h2[nt][1] = tanhf(c[1] + S.b2[c0 + 1]);
+            h2[nt][2] = tanhf(c[2] + S.b2[c0]);
+            h2[nt][3] = tanhf(c[3] + S.b2[c0 + 1]);
+            y0 = fmaf(S.w3[c0], h2[nt][0], fmaf(S.w3[c0 + 1], h2[nt][1], y0));
+            y1 = fmaf(S.w3[c0], h2[nt][2], fmaf(S.w3[c0 + 1], h2[nt][3], y1));
+        }
+        y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+        y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+        const float e0 = S.vld[r0] * (y0 + S.b3 - S.tgt[r0]), e1 = S.vld[r1] * (y1 + S.b3 - S.tgt[r1]);
+        const float gy0 = a.scale * e0, gy1 = a.scale * e1;
+        if (t == 0) {
+            lossa += (double)e0 * e0 + (double)e1 * e1;
+            db3a += gy0 + gy1;
+        }
+        // ---- G2 = gy w3 (1 - H2^2): A operand of G2 W2 and feature-major copy for dW2
+        uint32_t AG[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int c0 = 8 * nt + 2 * t;
+            dw3a[nt][0] = fmaf(gy0, h2[nt][0], fmaf(gy1, h2[nt][2], dw3a[nt][0]));
+            dw3a[nt][1] = fmaf(gy0, h2[nt][1], fmaf(gy1, h2[nt][3], dw3a[nt][1]));
+            const float wa = S.w3[c0], wb = S.w3[c0 + 1];
+            const uint32_t lo = pack_bf16x2(gy0 * wa * (1.f - h2[nt][0] * h2[nt][0]), gy0 * wb * (1.f - h2[nt][1] * h2[nt][1]));
+            const uint32_t hi = pack_bf16x2(gy1 * wa * (1.f - h2[nt][2] * h2[nt][2]), gy1 * wb * (1.f - h2[nt][3] * h2[nt][3]));
+            AG[nt >> 1][(nt & 1) * 2] = lo;
+            AG[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            S.G2T[c0][r0] = bf_lo(lo);
+            S.G2T[c0 + 1][r0] = bf_hi(lo);
+            S.G2T[c0][r1] = bf_lo(hi);
+            S.G2T[c0 + 1][r1] = bf_hi(hi);
+        }
+        // ---- G1 = (G2 W2) (1 - H1^2), feature-major copy for dW1
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt)
+                mma_bf16_16816(c, AG[kt][0], AG[kt][1], AG[kt][2], AG[kt][3], lds32(&S.W2T[8 * nt + g][16 * kt + 2 * t]),
+                               lds32(&S.W2T[8 * nt + g][16 * kt + 2 * t + 8]));
+            const int c0 = 8 * nt + 2 * t;
+            const uint32_t lo = pack_bf16x2(c[0] * h1[nt][0], c[1] * h1[nt][1]);
+            const uint32_t hi = pack_bf16x2(c[2] * h1[nt][2], c[3] * h1[nt][3]);
+            S.G1T[c0][r0] = bf_lo(lo);
+            S.G1T[c0 + 1][r0] = bf_hi(lo);
+            S.G1T[c0][r1] = bf_lo(hi);
+            S.G1T[c0 + 1][r1] = bf_hi(hi);
+        }
+    }
+    // warp sums of dw3 (over the rows, lane bits 2..4), db3 and the loss
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float v = dw3a[nt][q];
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            if (g == 0) S.dw3[w][8 * nt + 2 * t + q] = v;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        db3a += __shfl_xor_sync(0xffffffffu, db3a, o);
+        lossa += __shfl_xor_sync(0xffffffffu, lossa, o);
+    }
+    if (lane == 0) {
+        S.db3[w] = db3a;
+        S.loss[w] = lossa;
+    }
+    __syncthreads();
+
+    // ---- weight gradients over the block's samples: warp w owns rows j = 16 w .. 16 w + 15
+    float* part = a.part + (size_t)blockIdx.x * CL_N;
+    const int j0 = 16 * w + g, j1 = j0 + 8;
+#pragma unroll 1
+    for (int nt = 0; nt < 9; ++nt) {  // dW2 (k = 0..63) and db2 (k = 64)
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < kMB / 16; ++kt) {
+            const int m0 = 16 * kt + 2 * t;
+            mma_bf16_16816(c, lds32(&S.G2T[j0][m0]), lds32(&S.G2T[j1][m0]), lds32(&S.G2T[j0][m0 + 8]),
+                           lds32(&S.G2T[j1][m0 + 8]), lds32(&S.H1T[8 * nt + g][m0]), lds32(&S.H1T[8 * nt + g][m0 + 8]));
+        }
+        const int k0 = 8 * nt + 2 * t;
+        if (nt < 8) {
+            part[CL_W2 + 64 * j0 + k0] = c[0];
+            part[CL_W2 + 64 * j0 + k0 + 1] = c[1];
+            part[CL_W2 + 64 * j1 + k0] = c[2];
+            part[CL_W2 + 64 * j1 + k0 + 1] = c[3];
+        } else if (t == 0) {
+            part[CL_B2 + j0] = c[0];
+            part[CL_B2 + j1] = c[2];
+        }
+    }
+#pragma unroll 1
+    for (int nt = 0; nt < 2; ++nt) {  // dW1 (i = 0..8) and db1 (i = 9)
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < kMB / 16; ++kt) {
+            const int m0 = 16 * kt + 2 * t;
+            mma_bf16_16816(c, lds32(&S.G1T[j0][m0]), lds32(&S.G1T[j1][m0]), lds32(&S.G1T[j0][m0 + 8]),
+                           lds32(&S.G1T[j1][m0 + 8]), lds32(&S.XT[8 * nt + g][m0]), lds32(&S.XT[8 * nt + g][m0 + 8]));
+        }
+        const int i0 = 8 * nt + 2 * t;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = i0 + q;
+            if (i < 9) {
+                part[CL_W1 + 9 * j0 + i] = c[q];
+                part[CL_W1 + 9 * j1 + i] = c[2 + q];
+            } else if (i == 9) {
+                part[CL_B1 + j0] = c[q];
+                part[CL_B1 + j1] = c[2 + q];
+            }
+        }
+    }
+    if (tid < 64) part[CL_W3 + tid] = (S.dw3[0][tid] + S.dw3[1][tid]) + (S.dw3[2][tid] + S.dw3[3][tid]);
+    if (tid == 64) part[CL_B3] = (S.db3[0] + S.db3[1]) + (S.db3[2] + S.db3[3]);
+    if (tid == 65) a.part_loss[blockIdx.x] = (S.loss[0] + S.loss[1]) + (S.loss[2] + S.loss[3]);
+}
+
+// Second stage: sum of the block gradients in block order; the loss (fp64) is added to *loss.
+__device__ __forceinline__ float sum_blocks(const float* part, int blocks, int p)
+{
+    float s = 0.f;
+    for (int b = 0; b < blocks; ++b) s += part[(size_t)b * CL_N + p];
+    return s;
+}
+
+__global__ void k_cl_reduce_grad(const float* part, const double* part_loss, int blocks, float* grad, double* loss)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < CL_N) grad[p] = sum_blocks(part, blocks, p);
+    if (p == 0) {
+        double l = 0.0;
+        for (int b = 0; b < blocks; ++b) l += part_loss[b];
+        *loss += l;
     }
 }
 
-__global__ void k_cl_adam(float* w, float* m, float* v, float* grad, __nv_bfloat16* wb, float lr, float b1, float b2,
-                          float c1, float c2, float eps)
+// Adam (Kingma & Ba 2015) on fp32 master weights; the gradient is the sum of the block partials.
+__global__ void k_cl_reduce_adam(float* w, float* m, float* v, const float* part, const double* part_loss, int blocks,
+                                 double* loss, __nv_bfloat16* wb, float lr, float b1, float b2, float c1, float c2,
+                                 float eps)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {
+        double l = 0.0;
+        for (int b = 0; b < blocks; ++b) l += part_loss[b];
+        *loss += l;
+    }
     if (p >= CL_N) return;
-    const float g = grad[p];
+    const float g = sum_blocks(part, blocks, p);
     const float mm = b1 * m[p] + (1.f - b1) * g;
     const float vv = b2 * v[p] + (1.f - b2) * g * g;
     m[p] = mm;
@@ -264,28 +445,34 @@ __global__ void k_cl_adam(float* w, float* m, float* v, float* grad, __nv_bfloat
     const float wn = w[p] - lr * (mm * c1) / (sqrtf(vv * c2) + eps);
     w[p] = wn;
     wb[p] = __float2bfloat16_rn(wn);
-    grad[p] = 0.f;
 }
 
-__global__ void k_cl_stats(const float* X, const float* T, unsigned long long n, double* sums)
+// Column sums and sums of squares of the inputs and the target (column 9): per-block partials in
+// out[block][20], each block's in a fixed tree order, summed over blocks by the host in block order.
+constexpr int kStatBlocks = 256, kStatThreads = 256;
+
+__global__ void __launch_bounds__(kStatThreads) k_cl_stats(const float* X, const float* T, unsigned long long n,
+                                                            double* out)
 {
-    // sums[0..9] = sum of column, sums[10..19] = sum of squares (column 9 = target)
-    double s[10] = {0}, q[10] = {0};
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        for (int k = 0; k < 9; ++k) {
-            const double v = X[i * 9 + k];
+    __shared__ double sh[20][kStatThreads];
+    double s[20];
+    for (int k = 0; k < 20; ++k) s[k] = 0.0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * kStatThreads + threadIdx.x; i < n;
+         i += (unsigned long long)kStatBlocks * kStatThreads) {
+        for (int k = 0; k < 10; ++k) {
+            const double v = k < 9 ? X[i * 9 + k] : T[i];
             s[k] += v;
-            q[k] += v * v;
+            s[10 + k] += v * v;
         }
-        const double v = T[i];
-        s[9] += v;
-        q[9] += v * v;
     }
-    for (int k = 0; k < 10; ++k) {
-        atomicAdd(sums + k, s[k]);
-        atomicAdd(sums + 10 + k, q[k]);
+    for (int k = 0; k < 20; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = kStatThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < (unsigned)w)
+            for (int k = 0; k < 20; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x < 20) out[blockIdx.x * 20 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // splitmix64 (Steele, Lea & Flood 2014) for the initial weights and epoch orders
@@ -329,7 +516,9 @@ using namespace fpc;
 #define FPC_CL_CK(call, what)                                                                   \
     do {                                                                                        \
         cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess) return err(FPCLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+        if (e_ != cudaSuccess)                                                                  \
+            return err(e_ == cudaErrorMemoryAllocation ? FPCLBM_ERR_ALLOC : FPCLBM_ERR_CUDA,      \
+                       std::string(what) + ": " + cudaGetErrorString(e_));                        \
     } while (0)
 
 extern "C" int fpclbm_closure_sample(fpclbm_t h, int r, double tau_coarse, float* X, float* T, int on_device)
@@ -350,15 +539,15 @@ extern "C" int fpclbm_closure_sample(fpclbm_t h, int r, double tau_coarse, float
     const size_t nc = (size_t)cx * cy * cz;
     double* acc = nullptr;
     float *dX = X, *dT = T;
-    cudaError_t e = cudaMalloc(&acc, sizeof(double) * 10 * nc);
+    cudaError_t e = rt_malloc(&acc, sizeof(double) * 10 * nc);
     if (e == cudaSuccess && !on_device) {
-        e = cudaMalloc(&dX, sizeof(float) * 9 * nc);
-        if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(float) * nc);
+        e = rt_malloc(&dX, sizeof(float) * 9 * nc);
+        if (e == cudaSuccess) e = rt_malloc(&dT, sizeof(float) * nc);
     }
     if (e != cudaSuccess) {
-        cudaFree(acc);
+        rt_free(acc);
         if (!on_device) {
-            cudaFree(dX != X ? dX : nullptr);
+            rt_free(dX != X ? dX : nullptr);
         }
         return fail(h, FPCLBM_ERR_ALLOC, "closure_sample scratch");
     }
@@ -387,10 +576,10 @@ extern "C" int fpclbm_closure_sample(fpclbm_t h, int r, double tau_coarse, float
         if (e == cudaSuccess) e = cudaMemcpyAsync(T, dT, sizeof(float) * nc, cudaMemcpyDeviceToHost, h->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(acc);
+    rt_free(acc);
     if (!on_device) {
-        cudaFree(dX);
-        cudaFree(dT);
+        rt_free(dX);
+        rt_free(dT);
     }
     if (e != cudaSuccess) return fail(h, FPCLBM_ERR_CUDA, std::string("closure_sample: ") + cudaGetErrorString(e));
     return FPCLBM_OK;
@@ -398,17 +587,20 @@ extern "C" int fpclbm_closure_sample(fpclbm_t h, int r, double tau_coarse, float
 
 namespace {
 
-// Run fwd/bwd over `count` samples starting at epoch position `first`.
-cudaError_t run_batch(NetArgs a, cudaStream_t st)
+// Run the forward/backward kernel over `count` samples starting at epoch position `first`: one
+// block per kMB samples, each writing its gradient and loss to a.part / a.part_loss.
+int batch_blocks(unsigned long long count) { return (int)((count + kMB - 1) / kMB); }
+
+cudaError_t run_batch(const NetArgs& a, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * kSmemFloats;
+    const size_t smem = sizeof(TrainSmem);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_cl_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(k_cl_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
         attr = true;
     }
-    const unsigned blocks = (unsigned)((a.count + kB - 1) / kB);
-    k_cl_fwd_bwd<<<blocks, kB, smem, st>>>(a);
+    k_cl_mma<<<batch_blocks(a.count), kMB, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -420,16 +612,24 @@ extern "C" int fpclbm_closure_grad(const float* X, const float* T, int n, const 
     g_create_error.clear();
     if (!X || !T || !w || !grad || !loss || n < 1) return err(FPCLBM_ERR_ARG, "closure_grad: bad arguments");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int blocks = batch_blocks((unsigned long long)n);
     __nv_bfloat16* dW = nullptr;
-    float* dG = nullptr;
-    double* dL = nullptr;
-    cudaError_t e = cudaMalloc(&dW, sizeof(__nv_bfloat16) * CL_N);
-    if (e == cudaSuccess) e = cudaMalloc(&dG, sizeof(float) * CL_N);
-    if (e == cudaSuccess) e = cudaMalloc(&dL, sizeof(double));
+    float *dG = nullptr, *dP = nullptr;
+    double *dL = nullptr, *dPL = nullptr;
+    cudaError_t e = rt_malloc(&dW, sizeof(__nv_bfloat16) * CL_N);
+    if (e == cudaSuccess) e = rt_malloc(&dG, sizeof(float) * CL_N);
+    if (e == cudaSuccess) e = rt_malloc(&dL, sizeof(double));
+    if (e == cudaSuccess) e = rt_malloc(&dP, sizeof(float) * CL_N * (size_t)blocks);
+    if (e == cudaSuccess) e = rt_malloc(&dPL, sizeof(double) * (size_t)blocks);
+    auto cleanup = [&]() {
+        rt_free(dW);
+        rt_free(dG);
+        rt_free(dL);
+        rt_free(dP);
+        rt_free(dPL);
+    };
     if (e != cudaSuccess) {
-        cudaFree(dW);
-        cudaFree(dG);
-        cudaFree(dL);
+        cleanup();
         return err(FPCLBM_ERR_ALLOC, "closure_grad buffers");
     }
     NetArgs a;
@@ -447,18 +647,19 @@ extern "C" int fpclbm_closure_grad(const float* X, const float* T, int n, const 
     }
     a.scale = 2.0f / (float)n;
     a.W = dW;
-    a.grad = dG;
-    a.loss = dL;
+    a.part = dP;
+    a.part_loss = dPL;
     e = cudaMemcpyAsync(dW, w, sizeof(unsigned short) * CL_N, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dG, 0, sizeof(float) * CL_N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dL, 0, sizeof(double), st);
     if (e == cudaSuccess) e = run_batch(a, st);
+    if (e == cudaSuccess) {
+        k_cl_reduce_grad<<<(CL_N + 255) / 256, 256, 0, st>>>(dP, dPL, blocks, dG, dL);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad, dG, sizeof(float) * CL_N, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(loss, dL, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(dW);
-    cudaFree(dG);
-    cudaFree(dL);
+    cleanup();
     if (e != cudaSuccess) return err(FPCLBM_ERR_CUDA, std::string("closure_grad: ") + cudaGetErrorString(e));
     *loss /= n;
     return FPCLBM_OK;
@@ -474,13 +675,17 @@ extern "C" int fpclbm_closure_train(const float* X, const float* T, long long n,
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // standardisation of inputs and target
     double* dS = nullptr;
-    FPC_CL_CK(cudaMalloc(&dS, sizeof(double) * 20), "closure_train stats");
-    cudaMemsetAsync(dS, 0, sizeof(double) * 20, st);
-    k_cl_stats<<<256, 256, 0, st>>>(X, T, (unsigned long long)n, dS);
-    double sums[20];
-    cudaError_t e = cudaMemcpyAsync(sums, dS, sizeof sums, cudaMemcpyDeviceToHost, st);
+    FPC_CL_CK(rt_malloc(&dS, sizeof(double) * 20 * kStatBlocks), "closure_train stats");
+    k_cl_stats<<<kStatBlocks, kStatThreads, 0, st>>>(X, T, (unsigned long long)n, dS);
+    std::vector<double> parts(20 * kStatBlocks);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(parts.data(), dS, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(dS);
+    rt_free(dS);
+    double sums[20] = {0};
+    for (int b = 0; b < kStatBlocks; ++b)
+        for (int k = 0; k < 20; ++k) sums[k] += parts[20 * b + k];
     if (e != cudaSuccess) return err(FPCLBM_ERR_CUDA, std::string("closure_train stats: ") + cudaGetErrorString(e));
     double mu[10], sd[10];
     for (int k = 0; k < 10; ++k) {
@@ -498,22 +703,25 @@ extern "C" int fpclbm_closure_train(const float* X, const float* T, long long n,
     for (int i = 0; i < 64; ++i) w0[CL_W3 + i] = unif(1.0 / 8.0);
     std::vector<unsigned short> wb0(CL_N);
     for (int i = 0; i < CL_N; ++i) wb0[i] = bf16_bits(w0[i]);
-    float *dw = nullptr, *dm = nullptr, *dv = nullptr, *dg = nullptr;
+    const int max_blocks = batch_blocks((unsigned long long)std::min<long long>(batch, n));
+    float *dw = nullptr, *dm = nullptr, *dv = nullptr, *dP = nullptr;
     __nv_bfloat16* dwb = nullptr;
-    double* dL = nullptr;
-    e = cudaMalloc(&dw, sizeof(float) * CL_N);
-    if (e == cudaSuccess) e = cudaMalloc(&dm, sizeof(float) * CL_N);
-    if (e == cudaSuccess) e = cudaMalloc(&dv, sizeof(float) * CL_N);
-    if (e == cudaSuccess) e = cudaMalloc(&dg, sizeof(float) * CL_N);
-    if (e == cudaSuccess) e = cudaMalloc(&dwb, sizeof(__nv_bfloat16) * CL_N);
-    if (e == cudaSuccess) e = cudaMalloc(&dL, sizeof(double));
+    double *dL = nullptr, *dPL = nullptr;
+    e = rt_malloc(&dw, sizeof(float) * CL_N);
+    if (e == cudaSuccess) e = rt_malloc(&dm, sizeof(float) * CL_N);
+    if (e == cudaSuccess) e = rt_malloc(&dv, sizeof(float) * CL_N);
+    if (e == cudaSuccess) e = rt_malloc(&dP, sizeof(float) * CL_N * (size_t)max_blocks);
+    if (e == cudaSuccess) e = rt_malloc(&dPL, sizeof(double) * (size_t)max_blocks);
+    if (e == cudaSuccess) e = rt_malloc(&dwb, sizeof(__nv_bfloat16) * CL_N);
+    if (e == cudaSuccess) e = rt_malloc(&dL, sizeof(double));
     auto cleanup = [&]() {
-        cudaFree(dw);
-        cudaFree(dm);
-        cudaFree(dv);
-        cudaFree(dg);
-        cudaFree(dwb);
-        cudaFree(dL);
+        rt_free(dw);
+        rt_free(dm);
+        rt_free(dv);
+        rt_free(dP);
+        rt_free(dPL);
+        rt_free(dwb);
+        rt_free(dL);
     };
     if (e != cudaSuccess) {
         cleanup();
@@ -523,7 +731,6 @@ extern "C" int fpclbm_closure_train(const float* X, const float* T, long long n,
     if (e == cudaSuccess) e = cudaMemcpyAsync(dwb, wb0.data(), sizeof(unsigned short) * CL_N, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dm, 0, sizeof(float) * CL_N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dv, 0, sizeof(float) * CL_N, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dg, 0, sizeof(float) * CL_N, st);
     NetArgs a;
     std::memset(&a, 0, sizeof a);
     a.X = X;
@@ -534,8 +741,8 @@ extern "C" int fpclbm_closure_train(const float* X, const float* T, long long n,
         a.inv_sd[k] = (float)(1.0 / sd[k]);
     }
     a.W = dwb;
-    a.grad = dg;
-    a.loss = dL;
+    a.part = dP;
+    a.part_loss = dPL;
     const float b1 = 0.9f, b2 = 0.999f;
     long long step = 0;
     for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
@@ -555,7 +762,8 @@ extern "C" int fpclbm_closure_train(const float* X, const float* T, long long n,
             const float c1 = (float)(1.0 / (1.0 - std::pow((double)b1, (double)step)));
             const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, (double)step)));
             if (e == cudaSuccess) {
-                k_cl_adam<<<(CL_N + 255) / 256, 256, 0, st>>>(dw, dm, dv, dg, dwb, (float)lr, b1, b2, c1, c2, 1e-8f);
+                k_cl_reduce_adam<<<(CL_N + 255) / 256, 256, 0, st>>>(dw, dm, dv, dP, dPL, batch_blocks(a.count), dL, dwb,
+                                                                     (float)lr, b1, b2, c1, c2, 1e-8f);
                 e = cudaGetLastError();
             }
         }

@@ -41,6 +41,10 @@ namespace fpc {
 
 template <typename R>
 __device__ __forceinline__ R fmaR(R a, R b, R c) { return fma(a, b, c); }
+template <typename R>
+__device__ __forceinline__ R fminR(R a, R b) { return fmin(a, b); }
+template <typename R>
+__device__ __forceinline__ R fmaxR(R a, R b) { return fmax(a, b); }
 
 // Forward 3-point central-moment transform in deviation form (see header).
 template <typename R, bool K0>
@@ -206,7 +210,7 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
     }
 
     // shear rates, possibly corrected by the learned closure
-    if constexpr (MODE == MODE_LEARNED) {
+    if constexpr (learned_mode(MODE)) {
         R in[9];
         in[0] = FPC_D(2, 0, 0) - third * drho;  // kappa_200 - cs^2 rho
         in[1] = FPC_D(0, 2, 0) - third * drho;
@@ -219,11 +223,11 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
         in[8] = uz;
         const R dw = closure_delta_omega<R>(reinterpret_cast<const uint32_t*>(closure), in);
         const R lo = R(0.02), hi = R(1.98);
-        om4 = fmin(fmax(om4 + dw, lo), hi);
-        om5 = fmin(fmax(om5 + dw, lo), hi);
-        om6 = fmin(fmax(om6 + dw, lo), hi);
-        om8 = fmin(fmax(om8 + dw, lo), hi);
-        om9 = fmin(fmax(om9 + dw, lo), hi);
+        om4 = fminR(fmaxR(om4 + dw, lo), hi);
+        om5 = fminR(fmaxR(om5 + dw, lo), hi);
+        om6 = fminR(fmaxR(om6 + dw, lo), hi);
+        om8 = fminR(fmaxR(om8 + dw, lo), hi);
+        om9 = fminR(fmaxR(om9 + dw, lo), hi);
     }
 
     // Smagorinsky eddy viscosity (Sec. 4, turbulent channel LES): nu_t = c2 |S|, the strain rate

@@ -23,12 +23,14 @@ namespace fpc {
 // then their attractors plus half their sources (kappa + 1 (kappa^Mv - kappa)
 // + (1 - 1/2) sigma), with no grouping; without force the pre-collision
 // moments of those orders are not formed at all.
-enum { MODE_FP = 0, MODE_EQ = 1, MODE_LEARNED = 2, MODE_SMAG = 3, MODE_FP_R1 = 4, MODE_EQ_R1 = 5 };
+// MODE_LEARNED_R1 is the learned mode with the unit rates of orders 3-6.
+enum { MODE_FP = 0, MODE_EQ = 1, MODE_LEARNED = 2, MODE_SMAG = 3, MODE_FP_R1 = 4, MODE_EQ_R1 = 5, MODE_LEARNED_R1 = 6 };
 
 // FP or MCM attractors with the full register-cap / pipelined / paired variant set.
 __host__ __device__ constexpr bool plain_mode(int m) { return m == MODE_FP || m == MODE_EQ || m == MODE_FP_R1 || m == MODE_EQ_R1; }
 __host__ __device__ constexpr bool eq_mode(int m) { return m == MODE_EQ || m == MODE_EQ_R1; }
-__host__ __device__ constexpr bool r1_mode(int m) { return m == MODE_FP_R1 || m == MODE_EQ_R1; }
+__host__ __device__ constexpr bool r1_mode(int m) { return m == MODE_FP_R1 || m == MODE_EQ_R1 || m == MODE_LEARNED_R1; }
+__host__ __device__ constexpr bool learned_mode(int m) { return m == MODE_LEARNED || m == MODE_LEARNED_R1; }
 
 // Boundary kinds of the step kernel: periodic box; half-way bounce-back walls
 // at y = -1/2 and ny - 1/2 (x, z periodic); the same with the wall at

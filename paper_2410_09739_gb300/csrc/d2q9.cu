@@ -25,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "rtalloc.h"
 #include "collide.cuh"
 #include "fpclbm.h"
 #include "hostmem.h"
@@ -440,9 +441,9 @@ int fpclbm2d_create(fpclbm2d_t* out, int nx, int ny, int precision, void* cuda_s
     h->precision = precision;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     for (int j = 0; j < 9; ++j) h->omega[j] = 1.0;
-    cudaError_t e = cudaMalloc(&h->d_pop, 9ull * h->stride * esize2(precision));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_flag, sizeof(int));
+    cudaError_t e = rt_malloc(&h->d_pop, 9ull * h->stride * esize2(precision));
+    if (e == cudaSuccess) e = rt_malloc(&h->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = rt_malloc_host(&h->h_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemset(h->d_flag, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -459,9 +460,9 @@ int fpclbm2d_destroy(fpclbm2d_t h)
     if (!h) return FPCLBM_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph2(h);
-    if (h->d_pop) cudaFree(h->d_pop);
-    if (h->d_flag) cudaFree(h->d_flag);
-    if (h->h_flag) cudaFreeHost(h->h_flag);
+    if (h->d_pop) rt_free(h->d_pop);
+    if (h->d_flag) rt_free(h->d_flag);
+    if (h->h_flag) rt_free_host(h->h_flag);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
     return FPCLBM_OK;
@@ -487,14 +488,14 @@ int fpclbm2d_init_fields(fpclbm2d_t h, const double* rho, const double* ux, cons
         }
     }
     if (!on_device) {
-        FPC2_CK(h, cudaMalloc(&d, 3 * n * sizeof(double)), "staging");
+        FPC2_CK(h, rt_malloc(&d, 3 * n * sizeof(double)), "staging");
         cudaError_t ec = cudaMemcpyAsync(d, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         if (ec == cudaSuccess) ec = cudaMemcpyAsync(d + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         if (ec == cudaSuccess)
             ec = cudaMemcpyAsync(d + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         if (ec != cudaSuccess) {
             cudaStreamSynchronize(h->stream);
-            cudaFree(d);
+            rt_free(d);
             FPC2_CK(h, ec, "copy fields");
         }
         pr = d;
@@ -511,7 +512,7 @@ int fpclbm2d_init_fields(fpclbm2d_t h, const double* rho, const double* ux, cons
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (d) cudaFree(d);
+    if (d) rt_free(d);
     FPC2_CK(h, e, "init");
     h->steps = 0;
     h->initialized = true;
@@ -641,7 +642,7 @@ int fpclbm2d_moments(fpclbm2d_t h, double* rho, double* ux, double* uy, int on_d
         }
     }
     if (!on_device) {
-        FPC2_CK(h, cudaMalloc(&d, 3 * n * sizeof(double)), "staging");
+        FPC2_CK(h, rt_malloc(&d, 3 * n * sizeof(double)), "staging");
         for (int k = 0; k < 3; ++k) o[k] = o[k] ? d + k * n : nullptr;
     }
     const unsigned blocks = (h->ncells + 255) / 256;
@@ -658,7 +659,7 @@ int fpclbm2d_moments(fpclbm2d_t h, double* rho, double* ux, double* uy, int on_d
         for (int k = 0; k < 3 && e == cudaSuccess; ++k)
             if (host[k]) e = cudaMemcpyAsync(host[k], o[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (d) cudaFree(d);
+    if (d) rt_free(d);
     FPC2_CK(h, e, "moments");
     return FPCLBM_OK;
 }
@@ -674,7 +675,7 @@ int fpclbm2d_get_populations(fpclbm2d_t h, double* f)
     FPC2_CK(h, cudaMemcpyToSymbolAsync(c_slot2, slots, sizeof slots, 0, cudaMemcpyHostToDevice, h->stream), "slot table");
     const size_t n = h->ncells;
     double* d = nullptr;
-    FPC2_CK(h, cudaMalloc(&d, 9 * n * sizeof(double)), "staging");
+    FPC2_CK(h, rt_malloc(&d, 9 * n * sizeof(double)), "staging");
     const unsigned blocks = (h->ncells + 255) / 256;
     const int parity = (int)(h->steps & 1);
     switch (h->precision) {
@@ -686,7 +687,7 @@ int fpclbm2d_get_populations(fpclbm2d_t h, double* f)
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d);
+    rt_free(d);
     FPC2_CK(h, e, "get populations");
     return FPCLBM_OK;
 }
@@ -701,7 +702,7 @@ int fpclbm2d_set_populations(fpclbm2d_t h, const double* f)
     FPC2_CK(h, cudaMemcpyToSymbolAsync(c_slot2, slots, sizeof slots, 0, cudaMemcpyHostToDevice, h->stream), "slot table");
     const size_t n = h->ncells;
     double* d = nullptr;
-    FPC2_CK(h, cudaMalloc(&d, 9 * n * sizeof(double)), "staging");
+    FPC2_CK(h, rt_malloc(&d, 9 * n * sizeof(double)), "staging");
     cudaError_t e = cudaMemcpyAsync(d, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     const unsigned blocks = (h->ncells + 255) / 256;
     if (e == cudaSuccess) {
@@ -714,7 +715,7 @@ int fpclbm2d_set_populations(fpclbm2d_t h, const double* f)
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d);
+    rt_free(d);
     FPC2_CK(h, e, "set populations");
     h->steps = 0;  // written in the even-parity layout
     h->initialized = true;

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <vector>
 
+#include "rtalloc.h"
 #include "cell.cuh"
 #include "handle.h"
 
@@ -264,9 +265,9 @@ extern "C" int fpclbm_create_ensemble(fpclbm_t* out, int n_boxes, const int* dim
     int rc = alloc_common(h);
     cudaError_t e = cudaSuccess;
     if (rc == FPCLBM_OK) {
-        e = cudaMalloc(&h->d_pop, off * elem_size(precision));
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_ens_boxes, sizeof(EnsBox) * n_boxes);
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_tile_box, sizeof(unsigned) * tiles);
+        e = rt_malloc(&h->d_pop, off * elem_size(precision));
+        if (e == cudaSuccess) e = rt_malloc(&h->d_ens_boxes, sizeof(EnsBox) * n_boxes);
+        if (e == cudaSuccess) e = rt_malloc(&h->d_tile_box, sizeof(unsigned) * tiles);
         if (e == cudaSuccess) {
             std::vector<EnsBox> tab(n_boxes);
             std::vector<unsigned> tb(tiles);

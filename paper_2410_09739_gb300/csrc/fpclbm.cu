@@ -8,6 +8,7 @@
 // is autotuned on a saved copy of the state (the state is restored bit for
 // bit afterwards), and the choice is cached per device and configuration.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -16,6 +17,9 @@
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include "rtalloc.h"
+#include <nvtx3/nvToolsExt.h>
 
 #include "closure.cuh"
 #include "handle.h"
@@ -70,6 +74,35 @@ bool rates_valid(const double om[27], std::string& why)
     return true;
 }
 
+// Allocation wrappers (rtalloc.h): live-allocation count and the test hook's failure countdown
+// (-1: disarmed; k >= 0: the allocation after k more successful ones fails).
+std::atomic<long long> g_live_allocs{0};
+std::atomic<long long> g_fail_countdown{-1};
+
+cudaError_t rt_malloc_raw(void** p, size_t bytes, bool host)
+{
+    *p = nullptr;
+    long long c = g_fail_countdown.load();
+    while (c >= 0 && !g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 0) return cudaErrorMemoryAllocation;  // injected failure, as if the device were full
+    const cudaError_t e = host ? cudaMallocHost(p, bytes) : cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        ++g_live_allocs;
+    } else {
+        *p = nullptr;
+    }
+    return e;
+}
+
+void rt_free_raw(void* p, bool host)
+{
+    if (!p) return;
+    if (host) cudaFreeHost(p);
+    else cudaFree(p);
+    --g_live_allocs;
+}
+
 size_t elem_size(int precision)
 {
     switch (precision) {
@@ -84,17 +117,17 @@ int alloc_common(fpclbm* h)
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_flag, sizeof(int));
+    if (e == cudaSuccess) e = rt_malloc(&h->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = rt_malloc_host(&h->h_flag, sizeof(int));
     unsigned parts = 0;
     for (auto& b : h->boxes) {
         b.diag0 = parts;
         parts += (unsigned)diag_blocks(b.ncells);
     }
     h->diag_parts = parts;
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_part, sizeof(double) * 5 * (size_t)parts);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, sizeof(double) * 5);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_diag, sizeof(double) * 5);
+    if (e == cudaSuccess) e = rt_malloc(&h->d_part, sizeof(double) * 5 * (size_t)parts);
+    if (e == cudaSuccess) e = rt_malloc(&h->d_diag, sizeof(double) * 5);
+    if (e == cudaSuccess) e = rt_malloc_host(&h->h_diag, sizeof(double) * 5);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -202,12 +235,12 @@ bool has_force(const fpclbm* h) { return h->F[0] != 0.0 || h->F[1] != 0.0 || h->
 // their pre-collision values).
 int mode_of(const fpclbm* h)
 {
-    if (h->diffusion == FPCLBM_DIFF_FP_LEARNED) return MODE_LEARNED;
     if (h->diffusion == FPCLBM_DIFF_FP_SMAGORINSKY) return MODE_SMAG;
-    const int m = h->diffusion == FPCLBM_DIFF_EQUILIBRIUM ? MODE_EQ : MODE_FP;
+    const int m = h->diffusion == FPCLBM_DIFF_FP_LEARNED ? MODE_LEARNED
+                  : h->diffusion == FPCLBM_DIFF_EQUILIBRIUM ? MODE_EQ : MODE_FP;
     for (int j = 10; j < 27; ++j)
         if (h->omega[j] != 1.0) return m;
-    return m == MODE_EQ ? MODE_EQ_R1 : MODE_FP_R1;
+    return m == MODE_EQ ? MODE_EQ_R1 : m == MODE_LEARNED ? MODE_LEARNED_R1 : MODE_FP_R1;
 }
 
 // Boundary kind of the step kernel: a channel whose upper wall moves takes the
@@ -228,7 +261,7 @@ int upload_smag(fpclbm* h)
     const Box& b = h->boxes[0];
     const int ny = b.ny;
     if (!h->d_smag) {
-        cudaError_t e = cudaMalloc(&h->d_smag, sizeof(double) * (size_t)ny);
+        cudaError_t e = rt_malloc(&h->d_smag, sizeof(double) * (size_t)ny);
         if (e != cudaSuccess) return fail(h, FPCLBM_ERR_ALLOC, std::string("Smagorinsky table: ") + cudaGetErrorString(e));
     }
     const double nu = (1.0 / h->omega[4] - 0.5) / 3.0;
@@ -258,7 +291,7 @@ cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st, int block, int min
         return launch_ens_step((int)(t & 1), has_force(h), mode_of(h), make_ens_args(h), block, minb, grid, pipe, st);
     const StepArgs<double> a64 = make_args<double>(h);
     const StepArgs<float> a32 = make_args<float>(h);
-    StepLaunch cfg{block, minb, pipe};
+    StepLaunch cfg{block, minb, pipe, pipe == 3 ? grid : 3};  // variant 3 keeps its stage count in grid
     return launch_step(h->precision, (int)(t & 1), kernel_bc(h), has_force(h), mode_of(h), a64, a32, cfg, st);
 }
 
@@ -292,10 +325,10 @@ int build_graph(fpclbm* h)
 int ensure_stage(fpclbm* h, size_t bytes)
 {
     if (h->stage_bytes >= bytes) return FPCLBM_OK;
-    if (h->d_stage) cudaFree(h->d_stage);
+    if (h->d_stage) rt_free(h->d_stage);
     h->d_stage = nullptr;
     h->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&h->d_stage, bytes);
+    cudaError_t e = rt_malloc(&h->d_stage, bytes);
     if (e != cudaSuccess) return fail(h, FPCLBM_ERR_ALLOC, std::string("staging buffer: ") + cudaGetErrorString(e));
     h->stage_bytes = bytes;
     return FPCLBM_OK;
@@ -356,19 +389,35 @@ void save_tune_file()
     std::fclose(fp);
 }
 
-// FPCLBM_LAUNCH = "block:minb:variant" forces a single-box launch configuration
-// (variant 0: one cell per thread, 1: cp.async-pipelined, 2: two cells per thread).
+// FPCLBM_LAUNCH = "block:minb:variant[:stages]" forces a single-box launch configuration
+// (variant 0: one cell per thread, 1: cp.async-pipelined, 2: two cells per thread, 3: two cells
+// per thread through row-staged shared memory with `stages` stages, default 3).
 bool forced_launch(TuneChoice& c)
 {
     const char* v = std::getenv("FPCLBM_LAUNCH");
     if (!v || !v[0]) return false;
-    int b = 0, m = 0, p = 0;
-    if (std::sscanf(v, "%d:%d:%d", &b, &m, &p) != 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4 || p < 0 ||
-        p > 2)
+    int b = 0, m = 0, p = 0, ns = 3;
+    const int got = std::sscanf(v, "%d:%d:%d:%d", &b, &m, &p, &ns);
+    if (got < 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4 || p < 0 || p > 3 || ns < 3 || ns > 8)
         return false;
-    c = {b, m, 0, p};
+    c = {b, m, p == 3 ? ns : 0, p};
     return true;
 }
+
+// Whether the row-staged variant (stage.cuh) can run this handle: a single periodic box or
+// channel, fp32 arithmetic in the FP or MCM mode, 16- or 32-bit storage, rows of a multiple of
+// 16 bytes and at most 1024 cells, and three stages fitting the shared memory of a block.
+bool stage_ok(const fpclbm* h)
+{
+    if (h->ensemble || h->precision == FPCLBM_FP64) return false;
+    const int kb = kernel_bc(h);
+    if (!(kb == BC_PERIODIC || kb == BC_WALLS_Y) || !plain_mode(mode_of(h))) return false;
+    const Box& b = h->boxes[0];
+    const size_t es = elem_size(h->precision);
+    return (b.nx * es) % 16 == 0 && b.nx <= 1024 && 3 * 27 * b.nx * es + 24 <= 227 * 1024;
+}
+
+int stage_threads(const fpclbm* h) { return (h->boxes[0].nx / 2 + 31) / 32 * 32; }
 
 std::string tune_key(const fpclbm* h)
 {
@@ -410,8 +459,12 @@ int autotune(fpclbm* h)
         if (pipe_ok)
             for (int minb : {2, 3, 4}) cands.push_back({128, minb, 0, 1});
         if (pair_ok) cands.push_back({128, 2, 0, 2});  // 4 blocks of 128 threads, 128 registers
-    } else if (mode_of(h) == MODE_LEARNED && h->precision != FPCLBM_FP64 && fixed_walls) {
-        // capped at 128 registers first: twice the resident warps of the uncapped variant
+        if (stage_ok(h))  // row-staged paired variant with 3 or 4 shared-memory stages
+            for (int ns : {3, 4}) cands.push_back({stage_threads(h), 2, ns, 3});
+    } else if (learned_mode(mode_of(h)) && h->precision != FPCLBM_FP64 && fixed_walls) {
+        // two cells per thread first (the collision on the packed fp32 pipe, the MLP once per
+        // lane), then one cell per thread capped at 128 registers or uncapped
+        cands.push_back({128, 2, 0, 2});
         for (int minb : {2, 1})
             for (int block : {128, 256}) cands.push_back({block, minb, 0, 0});
     } else {
@@ -437,12 +490,17 @@ int autotune(fpclbm* h)
         return FPCLBM_OK;
     }
     if (!h->ensemble && forced_launch(forced)) {
-        if ((forced.pipe == 1 && !pipe_ok) || (forced.pipe == 2 && !pair_ok)) forced.pipe = 0;
-        if (forced.pipe == 2) forced.minb = 2;
-        if (!fp32_math && mode_of(h) != MODE_LEARNED) forced.minb = 1;  // learned: 1 or 2 (else 1)
+        if (forced.pipe == 3 && !stage_ok(h)) forced.pipe = pair_ok ? 2 : 0;
+        const bool pair_learned = learned_mode(mode_of(h)) && h->precision != FPCLBM_FP64 &&
+                                  (kb == BC_PERIODIC || kb == BC_WALLS_Y);
+        if ((forced.pipe == 1 && !pipe_ok) || (forced.pipe == 2 && !pair_ok && !pair_learned)) forced.pipe = 0;
+        if (forced.pipe == 2 || forced.pipe == 3) forced.minb = 2;
+        if (forced.pipe == 3) forced.block = stage_threads(h);
+        if (forced.pipe != 3) forced.grid = 0;
+        if (!fp32_math && !learned_mode(mode_of(h))) forced.minb = 1;  // learned: 1 or 2 (else 1)
         h->block = forced.block;
         h->minb = forced.minb;
-        h->grid = 0;
+        h->grid = forced.grid;
         h->pipe = forced.pipe;
         return FPCLBM_OK;
     }
@@ -467,7 +525,7 @@ int autotune(fpclbm* h)
     size_t bytes = 0;
     for (const Box& b : h->boxes) bytes += 27ull * b.stride * elem_size(h->precision);
     void* backup = nullptr;
-    if (cudaMalloc(&backup, bytes) != cudaSuccess) {
+    if (rt_malloc(&backup, bytes) != cudaSuccess) {
         cudaGetLastError();
         return FPCLBM_OK;  // no room to tune safely: keep the default
     }
@@ -501,7 +559,7 @@ int autotune(fpclbm* h)
     cudaError_t e = cudaStreamSynchronize(h->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(backup);
+    rt_free(backup);
     FPC_CK(h, e, "tune restore");
     h->block = win.block;
     h->minb = win.minb;
@@ -565,7 +623,7 @@ int fpclbm_create(fpclbm_t* out, int nx, int ny, int nz, int precision, int bc, 
     rates_from_params(1.0, 0.0, h->omega);
     int rc = alloc_common(h);
     if (rc == FPCLBM_OK) {
-        cudaError_t e = cudaMalloc(&h->d_pop, 27ull * stride * elem_size(precision));
+        cudaError_t e = rt_malloc(&h->d_pop, 27ull * stride * elem_size(precision));
         if (e != cudaSuccess) {
             g_create_error = std::string("populations: ") + cudaGetErrorString(e);
             rc = FPCLBM_ERR_ALLOC;
@@ -583,17 +641,17 @@ int fpclbm_destroy(fpclbm_t h)
 {
     if (!h) return FPCLBM_OK;
     drop_graph(h);
-    if (h->d_pop) cudaFree(h->d_pop);
-    if (h->d_flag) cudaFree(h->d_flag);
-    if (h->h_flag) cudaFreeHost(h->h_flag);
-    if (h->d_stage) cudaFree(h->d_stage);
-    if (h->d_part) cudaFree(h->d_part);
-    if (h->d_diag) cudaFree(h->d_diag);
-    if (h->h_diag) cudaFreeHost(h->h_diag);
-    if (h->d_closure) cudaFree(h->d_closure);
-    if (h->d_smag) cudaFree(h->d_smag);
-    if (h->d_ens_boxes) cudaFree(h->d_ens_boxes);
-    if (h->d_tile_box) cudaFree(h->d_tile_box);
+    if (h->d_pop) rt_free(h->d_pop);
+    if (h->d_flag) rt_free(h->d_flag);
+    if (h->h_flag) rt_free_host(h->h_flag);
+    if (h->d_stage) rt_free(h->d_stage);
+    if (h->d_part) rt_free(h->d_part);
+    if (h->d_diag) rt_free(h->d_diag);
+    if (h->h_diag) rt_free_host(h->h_diag);
+    if (h->d_closure) rt_free(h->d_closure);
+    if (h->d_smag) rt_free(h->d_smag);
+    if (h->d_ens_boxes) rt_free(h->d_ens_boxes);
+    if (h->d_tile_box) rt_free(h->d_tile_box);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return FPCLBM_OK;
@@ -749,7 +807,7 @@ int fpclbm_step(fpclbm_t h, long long n)
     if (n == 0) return FPCLBM_OK;
     {
         const int kb = kernel_bc(h), md = mode_of(h);
-        if (md == MODE_LEARNED && !(kb == BC_PERIODIC || kb == BC_WALLS_Y))
+        if (learned_mode(md) && !(kb == BC_PERIODIC || kb == BC_WALLS_Y))
             return fail(h, FPCLBM_ERR_ARG, "learned mode needs a periodic box or a channel with resting walls");
         if (md == MODE_SMAG && !bc_fixed(kb))
             return fail(h, FPCLBM_ERR_ARG, "Smagorinsky mode needs resting walls (no closed box, no moving wall)");
@@ -764,6 +822,12 @@ int fpclbm_step(fpclbm_t h, long long n)
         h->graph_valid = false;
     }
     FPC_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream), "flag reset");
+    // profiler ranges (NVTX, header-only: free unless a tool is attached) around the host-side
+    // issue of the step launches and graph replays
+    struct Range {
+        Range(const char* name) { nvtxRangePushA(name); }
+        ~Range() { nvtxRangePop(); }
+    } range("fpclbm_step");
     long long done = 0;
     // bring the AA parity to even with single launches
     while (done < n && ((h->steps + done) & 1)) {
@@ -775,6 +839,7 @@ int fpclbm_step(fpclbm_t h, long long n)
             int rc = build_graph(h);
             if (rc) return rc;
         }
+        Range replays("fpclbm_step graph replays");
         while (n - done >= kGraphSteps) {
             FPC_CK(h, cudaGraphLaunch(h->graph, h->stream), "graph launch");
             done += kGraphSteps;
@@ -787,6 +852,8 @@ int fpclbm_step(fpclbm_t h, long long n)
     h->steps += n;
     FPC_CK(h, cudaMemcpyAsync(h->h_flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag read");
     FPC_CK(h, cudaStreamSynchronize(h->stream), "step sync");
+    if (*h->h_flag & 2)
+        return fail(h, FPCLBM_ERR_TIMEOUT, "a step kernel's bounded wait for its staged data ran out");
     if (*h->h_flag) return fail(h, FPCLBM_ERR_DIVERGED, "a cell reached rho <= 0 or a non-finite value");
     return FPCLBM_OK;
 }
@@ -804,7 +871,7 @@ int fpclbm_get_launch(fpclbm_t h, int out[4])
     h->err.clear();
     if (!h->tuned) return fail(h, FPCLBM_ERR_STATE, "no launch chosen yet: the autotuner runs at the first step");
     out[0] = h->block;
-    out[1] = h->minb;
+    out[1] = h->pipe == 3 ? h->grid : h->minb;  // variant 3: its shared-memory stages
     out[2] = h->pipe;
     out[3] = mode_of(h);
     return FPCLBM_OK;
@@ -1022,7 +1089,7 @@ int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
     }
     pk[CP_B3] = wb(CL_B3) << 16;
     if (!h->d_closure) {
-        cudaError_t e = cudaMalloc(&h->d_closure, sizeof(uint32_t) * CP_WORDS);
+        cudaError_t e = rt_malloc(&h->d_closure, sizeof(uint32_t) * CP_WORDS);
         if (e != cudaSuccess) return fail(h, FPCLBM_ERR_ALLOC, "closure weights");
     }
     FPC_CK(h, cudaMemcpyAsync(h->d_closure, pk.data(), sizeof(uint32_t) * CP_WORDS, cudaMemcpyHostToDevice, h->stream),
@@ -1030,6 +1097,55 @@ int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
     FPC_CK(h, cudaStreamSynchronize(h->stream), "closure sync");
     h->have_closure = true;
     h->graph_valid = false;
+    return FPCLBM_OK;
+}
+
+int fpclbm_state_bytes(fpclbm_t h, unsigned long long* bytes)
+{
+    if (!h) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    if (!bytes) return fail(h, FPCLBM_ERR_ARG, "bytes is NULL");
+    unsigned long long n = 0;
+    for (const Box& b : h->boxes) n += 27ull * b.stride * elem_size(h->precision);
+    *bytes = n;
+    return FPCLBM_OK;
+}
+
+int fpclbm_get_state(fpclbm_t h, void* raw, unsigned long long bytes, long long* steps)
+{
+    if (!h) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    unsigned long long need = 0;
+    fpclbm_state_bytes(h, &need);
+    if (!raw || !steps) return fail(h, FPCLBM_ERR_ARG, "raw and steps must not be NULL");
+    if (bytes != need) return fail(h, FPCLBM_ERR_ARG, "raw state has " + std::to_string(need) + " bytes");
+    if (!h->initialized) return fail(h, FPCLBM_ERR_STATE, "populations not initialised");
+    FPC_CK(h, cudaMemcpyAsync(raw, h->d_pop, need, cudaMemcpyDeviceToHost, h->stream), "copy state");
+    FPC_CK(h, cudaStreamSynchronize(h->stream), "state sync");
+    *steps = h->steps;
+    return FPCLBM_OK;
+}
+
+int fpclbm_set_state(fpclbm_t h, const void* raw, unsigned long long bytes, long long steps)
+{
+    if (!h) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    unsigned long long need = 0;
+    fpclbm_state_bytes(h, &need);
+    if (!raw) return fail(h, FPCLBM_ERR_ARG, "raw is NULL");
+    if (bytes != need) return fail(h, FPCLBM_ERR_ARG, "raw state has " + std::to_string(need) + " bytes");
+    if (steps < 0) return fail(h, FPCLBM_ERR_ARG, "negative step count");
+    FPC_CK(h, cudaMemcpyAsync(h->d_pop, raw, need, cudaMemcpyHostToDevice, h->stream), "copy state");
+    FPC_CK(h, cudaStreamSynchronize(h->stream), "state sync");
+    h->steps = steps;
+    h->initialized = true;
+    return FPCLBM_OK;
+}
+
+int fpclbm_test_alloc_hook(int fail_after, long long* live)
+{
+    if (fail_after >= -1) g_fail_countdown.store(fail_after);
+    if (live) *live = g_live_allocs.load();
     return FPCLBM_OK;
 }
 

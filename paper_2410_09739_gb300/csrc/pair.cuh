@@ -33,7 +33,9 @@ __device__ __forceinline__ f2& operator-=(f2& a, f2 b) { return a = a - b; }
 __device__ __forceinline__ f2 operator/(f2 a, f2 b) { return f2(make_float2(a.v.x / b.v.x, a.v.y / b.v.y)); }
 __device__ __forceinline__ bool operator>(f2 a, f2 b) { return a.v.x > b.v.x && a.v.y > b.v.y; }
 __device__ __forceinline__ bool operator<(f2 a, f2 b) { return a.v.x < b.v.x && a.v.y < b.v.y; }
-// overload of collide.cuh's fmaR (a non-template exact match wins for f2)
+// overloads of collide.cuh's fmaR, fminR, fmaxR (a non-template exact match wins for f2)
+__device__ __forceinline__ f2 fminR(f2 a, f2 b) { return f2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y)); }
+__device__ __forceinline__ f2 fmaxR(f2 a, f2 b) { return f2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
 __device__ __forceinline__ f2 fmaR(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
 
 }  // namespace fpc

@@ -6,6 +6,7 @@
 #pragma once
 #include "cell.cuh"
 #include "internal.h"
+#include "stage.cuh"
 
 namespace fpc {
 
@@ -16,7 +17,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepArgs<R> a)
     bool active = true;
     if (cell >= a.ncells) {
         // the learned closure is warp-collective: tail lanes stay, on a valid cell, without writing
-        if (MODE != MODE_LEARNED) return;
+        if (!learned_mode(MODE)) return;
         active = false;
         cell = a.ncells - 1;
     }
@@ -149,8 +150,14 @@ cudaError_t step_go_pipe(const StepArgs<R>& a, cudaStream_t st)
 template <typename S, bool ODD, int BC, bool FORCE, int MODE, int MINB, bool ADJ>
 __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, unsigned half)
 {
-    const unsigned c1 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c1 >= half) return;
+    unsigned c1 = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = true;
+    if (c1 >= half) {
+        // the learned closure is warp-collective: tail lanes stay, on a valid pair, without writing
+        if (!learned_mode(MODE)) return;
+        active = false;
+        c1 = half - 1;
+    }
     CellGeom G;
     G.stride = a.stride;
     G.nx = a.nx;
@@ -161,15 +168,16 @@ __global__ void __launch_bounds__(128, MINB) k_step_pair(const StepArgs<f2> a, u
     const Rates<f2>& rt = a.rates;
     if constexpr (ODD && ADJ)  // neighbouring cells 2 c1, 2 c1 + 1 with a shared neighbour table
         update_pair_odd_adj<S, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, rt, a.Fx, a.Fy, a.Fz, rt.om[4],
-                                                rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag, a.lid6x, a.lid6z);
+                                                rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag, a.lid6x, a.lid6z,
+                                                a.closure, active);
     else if constexpr (ODD)  // cells c1 and c1 + half
         update_pair<S, ODD, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, half, a.ncells, rt, a.Fx, a.Fy, a.Fz,
                                              rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag, a.lid6x,
-                                             a.lid6z);
+                                             a.lid6z, a.closure, active);
     else  // neighbouring cells 2 c1 and 2 c1 + 1, vector loads and stores
         update_pair_even<S, BC, FORCE, MODE>(static_cast<S*>(a.buf), G, c1, a.ncells, rt, a.Fx, a.Fy, a.Fz,
                                              rt.om[4], rt.om[5], rt.om[6], rt.om[8], rt.om[9], a.flag, a.lid6x,
-                                             a.lid6z);
+                                             a.lid6z, a.closure, active);
 }
 
 // The launch arguments with every scalar duplicated into both lanes.
@@ -195,7 +203,7 @@ inline StepArgs<f2> pair_args(const StepArgs<float>& a)
         p.rates.src[j] = f2(a.rates.src[j], a.rates.src[j]);
     }
     p.flag = a.flag;
-    p.closure = nullptr;
+    p.closure = a.closure;
     p.smag = nullptr;
     return p;
 }
@@ -207,7 +215,7 @@ cudaError_t step_go_pair(const StepArgs<float>& a, cudaStream_t st)
     // the even step without force or moving wall (vector accesses, no neighbour table, no source
     // terms) fits in 96 registers without spilling: one block more per SM
     constexpr bool LID = BC == BC_WALLS_Y_LID || BC == BC_BOX_LID;
-    constexpr int BLOCKS = (ODD || FORCE || LID) ? 2 * MINB : 2 * MINB + 1;
+    constexpr int BLOCKS = learned_mode(MODE) ? 3 : (ODD || FORCE || LID) ? 2 * MINB : 2 * MINB + 1;
     const unsigned grid = (half + 127) / 128;
     // neighbouring cells on the odd step: nx even (rows hold whole pairs), no symmetry plane; the
     // closed box only with fp32 storage (its per-cell x-wall tests spill with 16-bit unpacking)
@@ -224,8 +232,18 @@ cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st
 {
     // paired variant: fp32 arithmetic, FP and MCM modes, every boundary kind, one register cap
     // (4 blocks of 128 threads: 128 registers hold two cells without spilling)
+    // the learned modes too, on periodic boxes and channels with resting walls (the paired MLP
+    // calls are warp-collective like the one-cell ones)
+    constexpr bool pair_learned = learned_mode(MODE) && (BC == BC_PERIODIC || BC == BC_WALLS_Y);
+    if constexpr (sizeof(R) == 4 && pair_learned && MINB == 2) {
+        if (cfg.pipe == 2) return step_go_pair<S, ODD, BC, FORCE, MODE, MINB>(a, st);
+    }
     if constexpr (sizeof(R) == 4 && plain_mode(MODE) && MINB == 2) {
         if (cfg.pipe == 2) return step_go_pair<S, ODD, BC, FORCE, MODE, MINB>(a, st);
+        // row-staged variant (stage.cuh): periodic boxes and channels
+        if constexpr (BC == BC_PERIODIC || BC == BC_WALLS_Y) {
+            if (cfg.pipe == 3) return step_go_stage<S, ODD, BC, FORCE, MODE>(a, cfg.stages, st);
+        }
     }
     // the pipelined variant retires tail lanes early, so it never runs the warp-collective
     // learned mode; it exists for the FP and MCM modes of periodic and channel boxes
@@ -246,7 +264,7 @@ template <typename S, typename R, bool ODD, int BC, bool FORCE, int MODE>
 cudaError_t step_by_minb(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st)
 {
     constexpr bool fp32_capped = sizeof(R) == 4 && plain_mode(MODE);
-    constexpr bool fp32_learned = sizeof(R) == 4 && MODE == MODE_LEARNED && bc_fixed(BC);
+    constexpr bool fp32_learned = sizeof(R) == 4 && learned_mode(MODE) && bc_fixed(BC);
     if constexpr (fp32_capped) {
         if (cfg.minb == 3) return step_go<S, R, ODD, BC, FORCE, MODE, 3>(a, cfg, st);
         if (cfg.minb == 4) return step_go<S, R, ODD, BC, FORCE, MODE, 4>(a, cfg, st);
@@ -270,6 +288,10 @@ cudaError_t step_by_mode(int mode, const StepArgs<R>& a, const StepLaunch& cfg, 
         case MODE_LEARNED:  // periodic and channel boxes (the closure's training data come from them)
             if constexpr (BC == BC_PERIODIC || BC == BC_WALLS_Y)
                 return step_by_minb<S, R, ODD, BC, FORCE, MODE_LEARNED>(a, cfg, st);
+            break;
+        case MODE_LEARNED_R1:  // the same with unit rates of orders 3-6
+            if constexpr (BC == BC_PERIODIC || BC == BC_WALLS_Y)
+                return step_by_minb<S, R, ODD, BC, FORCE, MODE_LEARNED_R1>(a, cfg, st);
             break;
         case MODE_SMAG:  // resting walls
             if constexpr (bc_fixed(BC)) return step_by_minb<S, R, ODD, BC, FORCE, MODE_SMAG>(a, cfg, st);

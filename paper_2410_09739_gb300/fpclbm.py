@@ -50,6 +50,7 @@ PRECISIONS = {"fp64": FPCLBM_FP64, "fp32": FPCLBM_FP32, "fp16": FPCLBM_FP32_STOR
 EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fpclbm_set_params",
             "fpclbm_set_rates", "fpclbm_set_force", "fpclbm_set_wall_velocity", "fpclbm_set_smagorinsky", "fpclbm_step", "fpclbm_moments", "fpclbm_diagnostics",
             "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_get_launch", "fpclbm_set_closure",
+            "fpclbm_state_bytes", "fpclbm_get_state", "fpclbm_set_state", "fpclbm_test_alloc_hook",
             "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc", "fpclbm_closure_sample",
             "fpclbm_closure_train", "fpclbm_closure_grad",
             "fpclbm2d_create", "fpclbm2d_init_fields", "fpclbm2d_set_params", "fpclbm2d_set_rates",
@@ -94,6 +95,10 @@ def load(path: str = LIB_PATH):
     L.fpclbm_set_populations.argtypes = [_P, _P]
     L.fpclbm_get_step_count.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong)]
     L.fpclbm_get_launch.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
+    L.fpclbm_state_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.fpclbm_get_state.argtypes = [_P, _P, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]
+    L.fpclbm_set_state.argtypes = [_P, _P, ctypes.c_ulonglong, ctypes.c_longlong]
+    L.fpclbm_test_alloc_hook.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     L.fpclbm_set_closure.argtypes = [_P, ctypes.POINTER(ctypes.c_ushort), ctypes.c_int]
     L.fpclbm_diagnostics_noalloc.argtypes = [_P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, _P, _P]
@@ -235,8 +240,38 @@ def fpclbm_get_step_count(h) -> int:
     return v.value
 
 
+def fpclbm_state_bytes(h) -> int:
+    v = ctypes.c_ulonglong()
+    _check(h, load().fpclbm_state_bytes(h, ctypes.byref(v)))
+    return v.value
+
+
+def fpclbm_get_state(h):
+    """(raw state as a uint8 numpy array, step count): the stored deviations in the storage type."""
+    raw = np.empty(fpclbm_state_bytes(h), dtype=np.uint8)
+    steps = ctypes.c_longlong()
+    _check(h, load().fpclbm_get_state(h, raw.ctypes.data_as(_P), raw.size, ctypes.byref(steps)))
+    return raw, steps.value
+
+
+def fpclbm_set_state(h, raw, steps: int):
+    raw = np.ascontiguousarray(raw)
+    if raw.dtype != np.uint8:
+        raise TypeError("raw state must be a uint8 array (as returned by fpclbm_get_state)")
+    return _check(h, load().fpclbm_set_state(h, raw.ctypes.data_as(_P), raw.size, int(steps)))
+
+
+def fpclbm_test_alloc_hook(fail_after: int = -2) -> int:
+    """Arm (fail_after >= 0) or disarm (-1) the injected allocation failure; returns the number of
+    live allocations of the library."""
+    live = ctypes.c_longlong()
+    load().fpclbm_test_alloc_hook(int(fail_after), ctypes.byref(live))
+    return live.value
+
+
 LAUNCH_MODES = {0: "FP", 1: "MCM", 2: "FP + learned closure", 3: "FP + Smagorinsky",
-                4: "FP, unit rates of orders 3-6", 5: "MCM, unit rates of orders 3-6"}
+                4: "FP, unit rates of orders 3-6", 5: "MCM, unit rates of orders 3-6",
+                6: "FP + learned closure, unit rates of orders 3-6"}
 
 
 def fpclbm_get_launch(h) -> dict:
@@ -251,10 +286,33 @@ def fpclbm_set_closure(h, bf16_bits):
     return _check(h, load().fpclbm_set_closure(h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_ushort)), w.size))
 
 
+def noalloc_args_check(f_numel: int, f_device: int, out_numel: int, out_device: int, current_device: int,
+                       ncells: int):
+    """Host-side checks of fpclbm_diagnostics_noalloc's buffers, made before any CUDA call: the C
+    entry point sees only raw pointers, so a cell count beyond the populations' length would make
+    its kernel read past the end of f.  Raises ValueError on a mismatch."""
+    ncells = int(ncells)
+    # counts outside [1, 2^31 - 1] are left to the library, which rejects them with FPCLBM_ERR_ARG
+    if 1 <= ncells <= 2 ** 31 - 1 and f_numel < 27 * ncells:
+        raise ValueError("f_dev holds %d values, fewer than 27 * ncells = %d" % (f_numel, 27 * ncells))
+    if out_numel < 5:
+        raise ValueError("out_dev holds %d values, needs 5" % out_numel)
+    if not (f_device == out_device == current_device):
+        raise ValueError("f_dev (cuda:%s) and out_dev (cuda:%s) must be on the current device cuda:%s"
+                         % (f_device, out_device, current_device))
+
+
 def fpclbm_diagnostics_noalloc(f_dev, ncells: int, Fx: float, Fy: float, Fz: float, out_dev, stream: int = 0):
     """Diagnostics of full populations already on the device, without any allocation by the
-    library: f_dev is a CUDA float64 tensor [27 * ncells] (alpha-major), out_dev a CUDA float64
-    tensor of 5.  Runs on `stream` (a cudaStream_t handle, 0 = default) and does not synchronise."""
+    library: f_dev is a CUDA float64 tensor of at least 27 * ncells values (alpha-major), out_dev
+    a CUDA float64 tensor of at least 5, both on the current device.  Runs on `stream` (a
+    cudaStream_t handle, 0 = default) and does not synchronise."""
+    import torch
+    for name, t in (("f_dev", f_dev), ("out_dev", out_dev)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("%s must be a CUDA torch tensor" % name)
+    noalloc_args_check(f_dev.numel(), f_dev.device.index, out_dev.numel(), out_dev.device.index,
+                       torch.cuda.current_device(), ncells)
     rc = load().fpclbm_diagnostics_noalloc(_ptr(f_dev, 1), int(ncells), float(Fx), float(Fy), float(Fz),
                                            _ptr(out_dev, 1), _P(stream) if stream else None)
     return _check(None, rc)
@@ -413,6 +471,12 @@ class Lattice:
 
     def launch(self) -> dict:
         return fpclbm_get_launch(self.h)
+
+    def get_state(self):
+        return fpclbm_get_state(self.h)
+
+    def set_state(self, raw, steps: int):
+        return fpclbm_set_state(self.h, raw, steps)
 
     def set_closure(self, bf16_bits):
         return fpclbm_set_closure(self.h, bf16_bits)

@@ -126,3 +126,19 @@ def test_other_entry_points_reject_bad_arguments_before_touching_the_device(lib)
     lib.fpclbm_last_error.restype = ctypes.c_char_p
     lib.fpclbm_last_error.argtypes = [P]
     assert b"finite" in lib.fpclbm_last_error(None)
+
+
+def test_noalloc_wrapper_checks_buffers_before_calling_the_library():
+    """fpclbm_diagnostics_noalloc's C entry point sees raw device pointers only; the wrapper checks
+    the populations' length against 27 * ncells, the result's length and the devices first."""
+    from paper_2410_09739_gb300 import fpclbm as F
+    ok = dict(f_numel=27 * 10, f_device=0, out_numel=5, out_device=0, current_device=0, ncells=10)
+    F.noalloc_args_check(**ok)
+    for bad in (dict(f_numel=27 * 10 - 1), dict(ncells=11), dict(out_numel=4), dict(f_device=1),
+                dict(out_device=1), dict(current_device=1)):
+        with pytest.raises(ValueError):
+            F.noalloc_args_check(**{**ok, **bad})
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):  # host tensors are not device pointers
+        F.fpclbm_diagnostics_noalloc(torch.zeros(27, dtype=torch.float64), 1, 0, 0, 0,
+                                     torch.zeros(5, dtype=torch.float64))

@@ -58,8 +58,32 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("n", [1, 64, 200])
+def _loss_and_grad_bf16_operands(theta, X, t):
+    """The training kernel's arithmetic: the operands of its tensor-core products (inputs x, first
+    hidden layer H1, and the back-propagated G2 = dL/dZ2 and G1 = dL/dZ1) rounded to bf16, products
+    exact here (fp32 accumulation on the GPU), tanh, the output layer, dL/dy and dw3 unrounded."""
+    p = C.unpack(theta)
+    n = X.shape[0]
+    xb, _ = bf16_round(X)
+    h1 = np.tanh(xb @ p["W1"].T + p["b1"])
+    h1b, _ = bf16_round(h1)
+    h2 = np.tanh(h1b @ p["W2"].T + p["b2"])
+    e = h2 @ p["W3"][0] + p["b3"][0] - t
+    gy = 2.0 / n * e
+    g2b, _ = bf16_round(gy[:, None] * p["W3"][0][None, :] * (1.0 - h2 * h2))
+    g1b, _ = bf16_round((g2b @ p["W2"]) * (1.0 - h1 * h1))
+    grads = {"W1": g1b.T @ xb, "b1": g1b.sum(0), "W2": g2b.T @ h1b, "b2": g2b.sum(0),
+             "W3": (gy @ h2)[None, :], "b3": np.array([gy.sum()])}
+    return float(np.mean(e * e)), grads
+
+
+@pytest.mark.parametrize("n", [1, 64, 200, 1000])
 def test_training_gradients_match_fp64_oracle(n):
+    """The training kernel's products are bf16 x bf16 -> fp32 tensor-core tiles (x, H1 and the
+    back-propagated G2, G1 rounded to bf16).  Against the exact fp64 oracle with the same bf16
+    weights the gradients meet the stated bound (relative 2-norm <= 2e-2 per tensor); against the
+    same arithmetic with those bf16 roundings they agree to fp32 accumulation (<= 1e-3: a bf16
+    rounding of an fp32-accumulated value can differ by one unit from that of the exact value)."""
     rng = np.random.default_rng(n)
     th = C.init_params(n)
     th[C.N_PARAMS - 65:C.N_PARAMS - 1] = rng.uniform(-0.3, 0.3, 64)  # non-zero last layer
@@ -69,11 +93,25 @@ def test_training_gradients_match_fp64_oracle(n):
     t = rng.normal(scale=0.3, size=n).astype(np.float32)
     loss, g = F.fpclbm_closure_grad(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), n, wbits)
     L, gr = C.loss_and_grad(wv, X.astype(np.float64), t.astype(np.float64))
-    assert abs(loss - L) <= 1e-5 * L
+    assert abs(loss - L) <= 2e-2 * L
     pg, pr = C.unpack(g.astype(np.float64)), C.unpack(gr)
+    Lb, pb = _loss_and_grad_bf16_operands(wv, X.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - Lb) <= 1e-5 * Lb
     for name, _ in C.SHAPES:
         assert _rel(pg[name], pr[name]) <= 2e-2, name
-        assert _rel(pg[name], pr[name]) <= 1e-4, name  # what fp32 accumulation actually gives
+        assert _rel(pg[name], pb[name].reshape(pg[name].shape)) <= 1e-3, name
+
+
+def test_training_is_deterministic():
+    """Block gradients are summed in a fixed order (no atomics): two trainings from the same seed
+    give the same weights bit for bit."""
+    n = 3000
+    rng = np.random.default_rng(8)
+    X = torch.from_numpy(rng.normal(scale=0.3, size=(n, 9)).astype(np.float32)).cuda()
+    t = torch.from_numpy((0.01 * rng.normal(size=n)).astype(np.float32)).cuda()
+    w1, l1 = F.fpclbm_closure_train(X, t, n, 3, 256, 1e-3, seed=4)
+    w2, l2 = F.fpclbm_closure_train(X, t, n, 3, 256, 1e-3, seed=4)
+    assert np.array_equal(w1, w2) and np.array_equal(l1, l2)
 
 
 def test_training_fits_a_smooth_target():
@@ -155,3 +193,38 @@ def test_learned_inference_matches_oracle():
     assert np.max(np.abs(got - ref)) <= 1e-6
     plain = O.step(fq, omega=O.rates(tau))
     assert np.max(np.abs(ref - plain)) > 1e-5  # the closure changed the step
+
+
+@pytest.mark.parametrize("launch", ["128:2:0", "128:2:2"])
+@pytest.mark.parametrize("drift", [0.0, 0.3])
+@pytest.mark.parametrize("shape", [(5, 4, 3), (8, 6, 5)])
+def test_learned_step_variants_match_oracle(monkeypatch, launch, drift, shape):
+    """The learned mode in both kernel variants (one cell per thread; two cells per thread with the
+    MLP run once per lane of the pair) and both rate settings (unit rates of orders 3-6, whose
+    moments are set to their attractors, and the order-scaled rates k * drift), over two steps
+    (both AA parities).  60 cells leave tail lanes in the warp-collective MLP; 240 cells with even
+    nx take the neighbouring-cell odd step.  Same 1e-6 per step as the one-step test."""
+    monkeypatch.setenv("FPCLBM_LAUNCH", launch)
+    nx, ny, nz = shape
+    rng = np.random.default_rng(19 + nx)
+    th = C.init_params(4) * 3.0
+    th[-65:-1] = rng.uniform(-0.05, 0.05, 64)
+    th[-1] = -0.05
+    wv, wbits = bf16_round(th)
+    rho, ux, uy, uz = W.random_fields(nx, ny, nz, seed=6, u_amp=0.05)
+    f0 = O.init_equilibrium(rho, ux, uy, uz) * (1 + 0.02 * rng.uniform(-1, 1, (27, nz, ny, nx)))
+    tau = 0.7
+    with F.Lattice(nx, ny, nz, "fp32") as lat:
+        lat.set_closure(wbits)
+        lat.set_params(tau, drift, F.FPCLBM_DIFF_FP_LEARNED)
+        lat.set_populations(f0)
+        fq = lat.get_populations()
+        ref = fq
+        for n in (1, 2):
+            lat.step(1)
+            got = lat.get_populations()
+            ref = _learned_step_oracle(ref, wv, O.rates(tau, drift))
+            assert np.max(np.abs(got - ref)) <= 1e-6 * n, n
+        lau = lat.launch()
+    assert lau["variant"] == int(launch[-1])
+    assert lau["mode"] == (6 if drift == 0.0 else 2)

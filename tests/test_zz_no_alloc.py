@@ -50,3 +50,13 @@ def test_noalloc_rejects_bad_sizes():
             F.fpclbm_diagnostics_noalloc(f, n, 0, 0, 0, out)
         assert e.value.code == F.FPCLBM_ERR_ARG
         assert "ncells" in F.fpclbm_last_error(None)
+
+
+def test_noalloc_rejects_too_short_buffers_before_any_launch():
+    torch = pytest.importorskip("torch")
+    f = torch.zeros(27 * 8, dtype=torch.float64, device="cuda")
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        F.fpclbm_diagnostics_noalloc(f, 9, 0, 0, 0, out)
+    with pytest.raises(ValueError):
+        F.fpclbm_diagnostics_noalloc(f, 8, 0, 0, 0, out[:4])
