@@ -286,8 +286,10 @@ FPCLBM_API int fpclbm_get_launch(fpclbm_t h, int out[4]);
 
 /* Install the learned closure used by FPCLBM_DIFF_FP_LEARNED: a per-cell
  * MLP 9 -> 64 -> 64 -> 1 (tanh hidden layers) whose inputs are the six
- * non-equilibrium second-order central moments and u, and whose output is
- * added to the shear rates omega_4,5,6,8,9 (clamped to (0, 2)).  Weights are
+ * non-equilibrium second-order central moments and u, and whose output
+ * delta omega corrects the shear rates omega_4,5,6,8,9 of the cell to
+ * max(omega + min(delta omega, 0), 0.02): the correction only adds viscosity,
+ * as the eddy-viscosity labels it is trained on do.  Weights are
  * bf16 bit patterns, n_params = 4865, in the order W1[64][9], b1[64],
  * W2[64][64], b2[64], W3[1][64], b3[1] (row-major, out x in).  No
  * counterpart in the paper, whose channel uses a Smagorinsky LES (Sec. 4).
@@ -311,7 +313,9 @@ FPCLBM_API int fpclbm_set_closure(fpclbm_t h, const unsigned short* bf16_weights
  *             tau_ij = <u_i u_j> - <u_i><u_j>.
  * <.> is the plain mean over the r^3 fine cells (rho, Step 7 velocity u,
  * u_i u_j); S_ij is the strain rate of <u> by central differences in coarse
- * cells (periodic in x, z; one-sided next to y walls).  Lattice velocities are
+ * cells (periodic in x, z; next to a y wall the derivative of the quadratic
+ * through the no-slip wall value 0 at y = -1/2 or ny/r - 1/2 and the two
+ * nearest rows: <u>_0 + <u>_1 / 3 at the first row).  Lattice velocities are
  * unchanged under acoustic scaling (dt/dx fixed), so features and labels are
  * in coarse lattice units.  Errors: ARG, STATE, ALLOC, CUDA. */
 FPCLBM_API int fpclbm_closure_sample(fpclbm_t fine, int r, double tau_coarse, float* X, float* T, int on_device);

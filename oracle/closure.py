@@ -138,6 +138,18 @@ def box_filter(field, r: int):
     return a.reshape(nz // r, r, ny // r, r, nx // r, r).mean(axis=(1, 3, 5))
 
 
+def wall_ddy(g):
+    """d/dy of a filtered field [nz, cy, nx] between no-slip walls at y = -1/2 and cy - 1/2 (coarse
+    units): central differences inside; at the first and last row the derivative of the quadratic
+    through the wall value 0 and the two nearest rows (y = -1/2, 0, 1: g_0 + g_1 / 3, mirrored at
+    the top), exact for quadratics that vanish at the walls."""
+    a = np.asarray(g, dtype=np.float64)
+    d = 0.5 * (np.roll(a, -1, axis=1) - np.roll(a, 1, axis=1))
+    d[:, 0, :] = a[:, 0, :] + a[:, 1, :] / 3.0
+    d[:, -1, :] = -(a[:, -1, :] + a[:, -2, :] / 3.0)
+    return d
+
+
 def sample(rho, ux, uy, uz, r: int, tau_c: float, walls_y: bool, cs2: float = 1.0 / 3.0):
     """Features [nc, 9] and labels [nc] of r^3 box-filtered fine fields (x fastest).
 
@@ -153,7 +165,7 @@ def sample(rho, ux, uy, uz, r: int, tau_c: float, walls_y: bool, cs2: float = 1.
 
     def ddx(g, d):
         if d == 1 and walls_y:
-            return np.gradient(g, axis=1)
+            return wall_ddy(g)
         return 0.5 * (np.roll(g, -1, axis=axes[d]) - np.roll(g, 1, axis=axes[d]))
 
     grad = [[ddx(ub[i], j) for j in range(3)] for i in range(3)]
@@ -170,7 +182,8 @@ def eddy_viscosity(ubar, uu_bar, walls_y: bool = True):
 
     ubar: (ux, uy, uz) filtered velocities [nz, ny, nx] (filter spacing = 1 coarse cell)
     uu_bar: dict (i, j) -> filtered u_i u_j for i <= j
-    Central differences, periodic in x and z; one-sided at the y ends when walls_y.
+    Central differences, periodic in x and z; at the y ends with walls_y the wall-aware derivative
+    of wall_ddy (the no-slip wall value 0 at y = -1/2 and cy - 1/2).
     """
     u = [np.asarray(c, dtype=np.float64) for c in ubar]
     axes = {0: 2, 1: 1, 2: 0}   # velocity direction -> array axis (x -> 2, y -> 1, z -> 0)
@@ -178,7 +191,7 @@ def eddy_viscosity(ubar, uu_bar, walls_y: bool = True):
     def ddx(f, d):
         ax = axes[d]
         if d == 1 and walls_y:
-            return np.gradient(f, axis=ax)
+            return wall_ddy(f)
         return 0.5 * (np.roll(f, -1, axis=ax) - np.roll(f, 1, axis=ax))
 
     grad = [[ddx(u[i], j) for j in range(3)] for i in range(3)]   # grad[i][j] = d u_i / d x_j

@@ -16,8 +16,12 @@ Steps (all simulation, filtering and training on the GPU through the C ABI):
      profile, and the wall-clock speed-up of the coarse run over the fine run
      for equal physical time on the same GPU.
 
-Usage: python -m paper_2410_09739_gb300.closure_study [--fine 384 192 192] [--r 4] ...
-Prints one JSON object.
+With --windows K the fine run continues through K successive collection windows after one
+spin-up, each with its own training and coarse runs: K independent estimates of the errors and
+their spread from one spin-up.
+
+Usage: python -m paper_2410_09739_gb300.closure_study [--fine 384 192 192] [--r 4] [--windows 2] ...
+Prints one JSON object (progress on stderr).
 """
 from __future__ import annotations
 
@@ -52,6 +56,9 @@ def parse(argv=None):
     p.add_argument("--precision", default="bf16")
     p.add_argument("--seed", type=int, default=7)
     p.add_argument("--cs", type=float, default=0.1, help="Smagorinsky constant of the non-learned baseline")
+    p.add_argument("--windows", type=int, default=1,
+                   help="successive collection windows of the same fine run, each with its own training and "
+                        "coarse runs (run-to-run spread)")
     p.add_argument("--vortices", type=float, default=0.0,
                    help="amplitude (units of u*) of large-scale streaks and streamwise vortices added to the "
                         "fine run's initial state to trigger transition (0: laminar profile and noise only)")
@@ -80,49 +87,23 @@ class Profile:
         return (self.sum / self.n).cpu().numpy()
 
 
-def run(args):
+def log(msg):
+    print("[closure_study %7.1f s] %s" % (time.perf_counter() - _T0, msg), file=sys.stderr, flush=True)
+
+
+_T0 = time.perf_counter()
+
+
+def window(fine, args, geo, seed):
+    """One collection window of the fine run (continuing it), training, and the coarse runs over the
+    same physical time.  Returns the window's record."""
     import torch
-    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream().cuda_stream
-    nxf, nyf, nzf = args.fine
-    r = args.r
-    Hf = nyf / 2.0
-    us = args.u_star
-    nu_f = us * Hf / args.re_tau
-    tau_f = 3.0 * nu_f + 0.5
-    Ff = us * us / Hf
-    Tf = Hf / us  # fine steps per friction time
-    nxc, nyc, nzc = nxf // r, nyf // r, nzf // r
-    nu_c = nu_f / r
-    tau_c = 3.0 * nu_c + 0.5
-    Fc = Ff * r
-    Tc = Tf / r
-    out = {"config": {"fine": [nxf, nyf, nzf], "coarse": [nxc, nyc, nzc], "r": r, "re_tau": args.re_tau,
-                      "u_star": us, "tau_fine": tau_f, "tau_coarse": tau_c, "F_fine": Ff, "F_coarse": Fc,
-                      "friction_time_fine_steps": Tf, "precision": args.precision,
-                      "spinup_T": args.spinup, "collect_T": args.collect, "snap_T": args.snap,
-                      "vortices_over_u_star": args.vortices, "seed": args.seed}}
-
-    # 1. fine spin-up
-    fine = F.Lattice(nxf, nyf, nzf, args.precision, F.FPCLBM_BC_WALLS_Y, stream=stream)
-    fine.set_params(tau_f)
-    fine.set_force(Ff, 0.0, 0.0)
-    rho0, ux0, uy0, uz0 = W.channel_fields(nxf, nyf, nzf, us, seed=args.seed)
-    if args.vortices > 0:
-        from paper_2410_09739_gb300.channel_les_study import perturbation
-        du, dv, dw = perturbation(nxf, nyf, nzf, nyf, args.vortices * us, full=True)
-        ux0, uy0, uz0 = ux0 + du, uy0 + dv, uz0 + dw
-    fine.init_fields(rho0, ux0, uy0, uz0)
-    n_spin = int(round(args.spinup * Tf))
-    t0 = time.perf_counter()
-    done = 0
-    while done < n_spin:
-        k = min(4096, n_spin - done)
-        fine.step(k)
-        done += k
-    spin_s = time.perf_counter() - t0
-
-    # 2. collection window
+    (nxf, nyf, nzf), (nxc, nyc, nzc), r = geo["fine"], geo["coarse"], geo["r"]
+    tau_c, Fc, Tf, Tc, us = geo["tau_c"], geo["F_c"], geo["T_f"], geo["T_c"], geo["u_star"]
+    out = {"seed": seed}
+    # collection window: every `snap` friction times filter the fine state onto r^3 blocks (features,
+    # labels) and accumulate the fine mean profile
     nc = nxc * nyc * nzc
     n_snap = max(1, int(round(args.collect / args.snap)))
     X = torch.empty((n_snap * nc, 9), dtype=torch.float32, device="cuda")
@@ -130,8 +111,7 @@ def run(args):
     snap_steps = int(round(args.snap * Tf))
     prof_f = Profile(torch, (nzf, nyf, nxf))
     X0 = None
-    fine_steps = 0
-    fine_s = 0.0
+    fine_steps, fine_s = 0, 0.0
     for s in range(n_snap):
         F.fpclbm_closure_sample(fine.h, r, tau_c, X[s * nc:(s + 1) * nc], T[s * nc:(s + 1) * nc], on_device=1)
         if s == 0:
@@ -144,23 +124,23 @@ def run(args):
         fine_steps += snap_steps
     prof_f.add(fine)
     U_fine = prof_f.mean().reshape(nyc, r).mean(axis=1)  # filtered onto coarse rows
-    fine.close()
+    log("window %d: %d fine steps collected in %.1f s" % (seed, fine_steps, fine_s))
 
-    # 3. training
+    # training on the window's samples
     t0 = time.perf_counter()
-    w, losses = F.fpclbm_closure_train(X, T, n_snap * nc, args.epochs, args.batch, args.lr, seed=args.seed,
+    w, losses = F.fpclbm_closure_train(X, T, n_snap * nc, args.epochs, args.batch, args.lr, seed=seed,
                                        stream=stream)
     train_s = time.perf_counter() - t0
     labels = T.cpu().numpy()
     out["training"] = {"samples": n_snap * nc, "epochs": args.epochs, "loss_first": float(losses[0]),
                        "loss_last": float(losses[-1]), "seconds": train_s,
                        "label_mean": float(labels.mean()), "label_min": float(labels.min())}
+    del X, T
 
-    # 4. coarse runs from the filtered velocity at the start of the window
+    # coarse runs from the filtered velocity at the start of the window
     u0 = X0[:, 6:9].double().cpu().numpy()
     fields = (np.ones(nc), np.ascontiguousarray(u0[:, 0]), np.ascontiguousarray(u0[:, 1]),
               np.ascontiguousarray(u0[:, 2]))
-    n_coarse = int(round(n_snap * args.snap * Tc))
     coarse_res = {}
     for name in ("plain", "learned", "smagorinsky"):
         lat = F.Lattice(nxc, nyc, nzc, args.precision, F.FPCLBM_BC_WALLS_Y, stream=stream)
@@ -195,13 +175,82 @@ def run(args):
         lat.close()
     out["U_fine_filtered"] = [float(v) for v in U_fine]
     out["coarse"] = coarse_res
-    # 5. speed-up for equal physical time (per friction time)
+    # speed-up for equal physical time (per friction time)
     fine_per_T = fine_s / (fine_steps / Tf)
     for name, res in coarse_res.items():
         if res["steps"]:
             res["speedup_vs_fine"] = fine_per_T / (res["seconds"] / (res["steps"] / Tc))
-    out["fine"] = {"spinup_seconds": spin_s, "collect_seconds": fine_s, "collect_steps": fine_steps,
-                   "seconds_per_friction_time": fine_per_T}
+    out["fine"] = {"collect_seconds": fine_s, "collect_steps": fine_steps, "seconds_per_friction_time": fine_per_T}
+    log("window %d: errors %s" % (seed, {k: v["profile_l2_rel_error"] for k, v in coarse_res.items()}))
+    return out
+
+
+def run(args):
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    nxf, nyf, nzf = args.fine
+    r = args.r
+    Hf = nyf / 2.0
+    us = args.u_star
+    nu_f = us * Hf / args.re_tau
+    tau_f = 3.0 * nu_f + 0.5
+    Ff = us * us / Hf
+    Tf = Hf / us  # fine steps per friction time
+    nxc, nyc, nzc = nxf // r, nyf // r, nzf // r
+    nu_c = nu_f / r
+    tau_c = 3.0 * nu_c + 0.5
+    Fc = Ff * r
+    Tc = Tf / r
+    geo = {"fine": (nxf, nyf, nzf), "coarse": (nxc, nyc, nzc), "r": r, "tau_c": tau_c, "F_c": Fc, "T_f": Tf,
+           "T_c": Tc, "u_star": us}
+    out = {"config": {"fine": [nxf, nyf, nzf], "coarse": [nxc, nyc, nzc], "r": r, "re_tau": args.re_tau,
+                      "u_star": us, "tau_fine": tau_f, "tau_coarse": tau_c, "F_fine": Ff, "F_coarse": Fc,
+                      "friction_time_fine_steps": Tf, "precision": args.precision,
+                      "spinup_T": args.spinup, "collect_T": args.collect, "snap_T": args.snap,
+                      "windows": args.windows, "vortices_over_u_star": args.vortices, "seed": args.seed,
+                      "epochs": args.epochs, "batch": args.batch, "lr": args.lr, "cs": args.cs}}
+
+    # fine spin-up
+    fine = F.Lattice(nxf, nyf, nzf, args.precision, F.FPCLBM_BC_WALLS_Y, stream=stream)
+    fine.set_params(tau_f)
+    fine.set_force(Ff, 0.0, 0.0)
+    rho0, ux0, uy0, uz0 = W.channel_fields(nxf, nyf, nzf, us, seed=args.seed)
+    if args.vortices > 0:
+        from paper_2410_09739_gb300.channel_les_study import perturbation
+        du, dv, dw = perturbation(nxf, nyf, nzf, nyf, args.vortices * us, full=True)
+        ux0, uy0, uz0 = ux0 + du, uy0 + dv, uz0 + dw
+    fine.init_fields(rho0, ux0, uy0, uz0)
+    del rho0, ux0, uy0, uz0
+    n_spin = int(round(args.spinup * Tf))
+    t0 = time.perf_counter()
+    done = 0
+    while done < n_spin:
+        k = min(4096, n_spin - done)
+        fine.step(k)
+        done += k
+        if done % (8 * 4096) == 0 or done == n_spin:
+            log("spin-up %d / %d fine steps" % (done, n_spin))
+    out["spinup_seconds"] = time.perf_counter() - t0
+
+    # successive windows of the same fine run: one training and one set of coarse runs each
+    wins = [window(fine, args, geo, args.seed + k) for k in range(args.windows)]
+    fine.close()
+    out["windows"] = wins
+    # the first window under the keys of a single-window study
+    out["U_fine_filtered"], out["coarse"], out["training"] = wins[0]["U_fine_filtered"], wins[0]["coarse"], \
+        wins[0]["training"]
+    out["fine"] = wins[0]["fine"]
+    summ = {}
+    for name in ("plain", "learned", "smagorinsky"):
+        errs = [w["coarse"][name]["profile_l2_rel_error"] for w in wins]
+        errs = [e for e in errs if e is not None]
+        sp = [w["coarse"][name].get("speedup_vs_fine") for w in wins]
+        sp = [v for v in sp if v]
+        summ[name] = {"errors": errs, "mean_error": float(np.mean(errs)) if errs else None,
+                      "spread": float(np.max(errs) - np.min(errs)) if errs else None,
+                      "mean_speedup_vs_fine": float(np.mean(sp)) if sp else None}
+    out["summary"] = summ
     return out
 
 

@@ -71,8 +71,8 @@ __global__ void k_cl_filter(FilterArgs a)
 }
 
 // Strain rate of the filtered velocity (central differences in coarse cells,
-// periodic in x and z, periodic or one-sided at y walls), eddy viscosity from
-// the sub-filter stress, label and features.
+// periodic in x and z, periodic in y or, at y walls, through the no-slip wall
+// value), eddy viscosity from the sub-filter stress, label and features.
 __global__ void k_cl_label(const double* __restrict__ acc, int cx, int cy, int cz, int walls, double tau_c,
                            float* X, float* T)
 {
@@ -89,12 +89,14 @@ __global__ void k_cl_label(const double* __restrict__ acc, int cx, int cy, int c
         const int q = 1 + i;
         gr[i][0] = 0.5 * (at(q, (x + 1) % cx, y, z) - at(q, (x - 1 + cx) % cx, y, z));
         gr[i][2] = 0.5 * (at(q, x, y, (z + 1) % cz) - at(q, x, y, (z - 1 + cz) % cz));
+        // next to a no-slip wall (y = -1/2 or cy - 1/2) the derivative of the quadratic through the
+        // wall value 0 and the two nearest rows
         if (!walls)
             gr[i][1] = 0.5 * (at(q, x, (y + 1) % cy, z) - at(q, x, (y - 1 + cy) % cy, z));
         else if (y == 0)
-            gr[i][1] = at(q, x, 1, z) - at(q, x, 0, z);
+            gr[i][1] = at(q, x, 0, z) + at(q, x, 1, z) / 3.0;
         else if (y == cy - 1)
-            gr[i][1] = at(q, x, cy - 1, z) - at(q, x, cy - 2, z);
+            gr[i][1] = -(at(q, x, cy - 1, z) + at(q, x, cy - 2, z) / 3.0);
         else
             gr[i][1] = 0.5 * (at(q, x, y + 1, z) - at(q, x, y - 1, z));
     }

@@ -221,13 +221,15 @@ __device__ __forceinline__ bool collide_cell(R (&g)[27], const Rates<R>& rt, R F
         in[6] = ux;
         in[7] = uy;
         in[8] = uz;
-        const R dw = closure_delta_omega<R>(reinterpret_cast<const uint32_t*>(closure), in);
-        const R lo = R(0.02), hi = R(1.98);
-        om4 = fminR(fmaxR(om4 + dw, lo), hi);
-        om5 = fminR(fmaxR(om5 + dw, lo), hi);
-        om6 = fminR(fmaxR(om6 + dw, lo), hi);
-        om8 = fminR(fmaxR(om8 + dw, lo), hi);
-        om9 = fminR(fmaxR(om9 + dw, lo), hi);
+        // the correction adds an eddy viscosity nu_t >= 0 (the training label's definition), so it
+        // only lowers the rates: omega + min(delta omega, 0), kept above 0.02
+        const R dw = fminR(closure_delta_omega<R>(reinterpret_cast<const uint32_t*>(closure), in), R(0));
+        const R lo = R(0.02);
+        om4 = fmaxR(om4 + dw, lo);
+        om5 = fmaxR(om5 + dw, lo);
+        om6 = fmaxR(om6 + dw, lo);
+        om8 = fmaxR(om8 + dw, lo);
+        om9 = fmaxR(om9 + dw, lo);
     }
 
     // Smagorinsky eddy viscosity (Sec. 4, turbulent channel LES): nu_t = c2 |S|, the strain rate

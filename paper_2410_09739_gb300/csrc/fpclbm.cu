@@ -291,7 +291,7 @@ cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st, int block, int min
         return launch_ens_step((int)(t & 1), has_force(h), mode_of(h), make_ens_args(h), block, minb, grid, pipe, st);
     const StepArgs<double> a64 = make_args<double>(h);
     const StepArgs<float> a32 = make_args<float>(h);
-    StepLaunch cfg{block, minb, pipe, pipe == 3 ? grid : 3};  // variant 3 keeps its stage count in grid
+    StepLaunch cfg{block, minb, pipe, pipe == 3 ? grid : 2};  // variant 3 keeps its stage count in grid
     return launch_step(h->precision, (int)(t & 1), kernel_bc(h), has_force(h), mode_of(h), a64, a32, cfg, st);
 }
 
@@ -391,14 +391,14 @@ void save_tune_file()
 
 // FPCLBM_LAUNCH = "block:minb:variant[:stages]" forces a single-box launch configuration
 // (variant 0: one cell per thread, 1: cp.async-pipelined, 2: two cells per thread, 3: two cells
-// per thread through row-staged shared memory with `stages` stages, default 3).
+// per thread through row-staged shared memory with `stages` input stages, 2..6, default 2).
 bool forced_launch(TuneChoice& c)
 {
     const char* v = std::getenv("FPCLBM_LAUNCH");
     if (!v || !v[0]) return false;
-    int b = 0, m = 0, p = 0, ns = 3;
+    int b = 0, m = 0, p = 0, ns = 2;
     const int got = std::sscanf(v, "%d:%d:%d:%d", &b, &m, &p, &ns);
-    if (got < 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4 || p < 0 || p > 3 || ns < 3 || ns > 8)
+    if (got < 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4 || p < 0 || p > 3 || ns < 2 || ns > 6)
         return false;
     c = {b, m, p == 3 ? ns : 0, p};
     return true;
@@ -406,7 +406,7 @@ bool forced_launch(TuneChoice& c)
 
 // Whether the row-staged variant (stage.cuh) can run this handle: a single periodic box or
 // channel, fp32 arithmetic in the FP or MCM mode, 16- or 32-bit storage, rows of a multiple of
-// 16 bytes and at most 1024 cells, and three stages fitting the shared memory of a block.
+// 16 bytes and at most 512 cells (tiles of 256 or 512 cells).
 bool stage_ok(const fpclbm* h)
 {
     if (h->ensemble || h->precision == FPCLBM_FP64) return false;
@@ -414,10 +414,11 @@ bool stage_ok(const fpclbm* h)
     if (!(kb == BC_PERIODIC || kb == BC_WALLS_Y) || !plain_mode(mode_of(h))) return false;
     const Box& b = h->boxes[0];
     const size_t es = elem_size(h->precision);
-    return (b.nx * es) % 16 == 0 && b.nx <= 1024 && 3 * 27 * b.nx * es + 24 <= 227 * 1024;
+    return (b.nx * es) % 16 == 0 && b.nx <= 512;
 }
 
-int stage_threads(const fpclbm* h) { return (h->boxes[0].nx / 2 + 31) / 32 * 32; }
+// Threads of a row-staged block: 4 or 8 consumer warps and one producer warp.
+int stage_threads(const fpclbm* h) { return h->boxes[0].nx <= 256 ? 160 : 288; }
 
 std::string tune_key(const fpclbm* h)
 {
@@ -459,8 +460,8 @@ int autotune(fpclbm* h)
         if (pipe_ok)
             for (int minb : {2, 3, 4}) cands.push_back({128, minb, 0, 1});
         if (pair_ok) cands.push_back({128, 2, 0, 2});  // 4 blocks of 128 threads, 128 registers
-        if (stage_ok(h))  // row-staged paired variant with 3 or 4 shared-memory stages
-            for (int ns : {3, 4}) cands.push_back({stage_threads(h), 2, ns, 3});
+        if (stage_ok(h))  // row-staged paired variant with 2 or 3 input stages
+            for (int ns : {2, 3}) cands.push_back({stage_threads(h), 2, ns, 3});
     } else if (learned_mode(mode_of(h)) && h->precision != FPCLBM_FP64 && fixed_walls) {
         // two cells per thread first (the collision on the packed fp32 pipe, the MLP once per
         // lane), then one cell per thread capped at 128 registers or uncapped

@@ -15,7 +15,7 @@ struct StepLaunch {
     int pipe = 0;  // 1: software-pipelined persistent variant (cp.async prefetch), 4/8-byte storage only;
                    // 2: paired variant (two cells per thread on the packed fp32 pipe);
                    // 3: row-staged paired variant (bulk copies of whole slot rows through shared memory)
-    int stages = 3;  // variant 3: shared-memory stages per block (3..8)
+    int stages = 2;  // variant 3: shared-memory input stages per block (2..6)
 };
 
 // One time step of a single box.  odd selects the AA-pattern parity (0: own

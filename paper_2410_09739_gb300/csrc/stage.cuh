@@ -1,51 +1,51 @@
 // stage.cuh -- row-staged variant of the paired step kernel (launch variant 3).
 //
-// One tile is one x-row of the box (fixed y, z), all 27 slots.  A persistent
-// CTA walks the rows t = blockIdx.x + k gridDim.x through a ring of ns
-// shared-memory stages, each holding the 27 slot rows of one tile:
+// A tile is R whole x-rows of the box (rows y0 .. y0+R-1 of one plane z, all
+// 27 slots).  Each CTA is a warp-specialised pipeline over the tiles
+// t = blockIdx.x + k gridDim.x:
 //
-//   load   one elected thread moves the 27 source rows of a tile into a
-//          stage with bulk asynchronous copies (cp.async.bulk, completion
-//          counted in bytes on the stage's mbarrier).  Even step: the cell's
-//          own slot rows.  Odd step: for slot s the row (y - e_y, z - e_z) of
-//          slot 26 - s, i.e. the row the populations stream in from (Step 6);
-//          where that row lies in a wall (half-way bounce-back at y = -1/2 or
-//          ny - 1/2) the tile's own row of slot s, which holds the reflected
-//          value the even step parked there (the AA pattern of cell.cuh).
-//   compute  every thread takes two neighbouring cells x, x + 1 of the row,
-//          reads its 27 value pairs from the stage (the x - e_x shift and the
-//          periodic x wrap are shared-memory indices), collides them with the
-//          packed fp32 arithmetic of pair.cuh (the same collide_cell as the
-//          paired kernel, so the results are bit-identical to it), and writes
-//          each post-collision value back into the stage at its streamed
-//          position x + e_x (odd step; the cell itself where the link meets a
-//          wall) or in place (even step);
-//   store  the elected thread bulk-stores the 27 rows to their destination
-//          rows: even step the tile's own row of slot 26 - s; odd step the row
-//          (y + e_y, z + e_z) of slot s, or the tile's own row of slot 26 - s
-//          for a link into a wall.
+//   producer warp   lane s (s < 27) moves slot s: bulk asynchronous copies
+//                   (cp.async.bulk) of the tile's source rows into an input
+//                   stage, completion counted in bytes on the stage's "full"
+//                   mbarrier, and, once the consumers have filled an output
+//                   stage, bulk copies of its rows to their destinations.
+//                   Even step: the cells' own rows of slot s in, of slot
+//                   26 - s out.  Odd step: in, the rows y - e_y of slot 26 - s
+//                   (where the populations stream from, Step 6), or the own row
+//                   of slot s where that row lies in a y wall; out, the rows
+//                   y + e_y of slot s, or the own row of slot 26 - s for a link
+//                   into a wall (half-way bounce-back, the AA pattern of
+//                   cell.cuh).  Periodic wrap in y and z.
+//   consumer warps  every thread takes two neighbouring cells x, x + 1 of a
+//                   row, reads its 27 value pairs from the input stage (the
+//                   x - e_x shift and the periodic x wrap are shared-memory
+//                   indices), releases the stage, collides the pair with the
+//                   packed fp32 arithmetic of pair.cuh (the same collide_cell
+//                   as the paired kernel: results bit-identical to it), and
+//                   writes each post-collision value into the output stage at
+//                   its streamed position x + e_x (odd step; the cell itself
+//                   for a link into a wall) or in place (even step).
 //
-// The AA pattern makes this race-free: within one step the rows a tile reads
-// are exactly the rows it writes, and no other tile touches them.  A stage is
-// reloaded only after the bulk store that reads it has finished reading
-// (cp.async.bulk.wait_group.read).  While a tile is computed the loads of the
-// next ns - 2 tiles are in flight.
+// Handshakes (no block-wide barrier after set-up): full_in (producer -> the
+// consumers: data arrived), empty_in (consumers -> producer: stage read),
+// full_out (consumers -> producer: output written), empty_out (producer ->
+// consumers: the bulk store has read the output stage).  The AA pattern makes
+// the in-place update race-free across tiles: within one step the rows a tile
+// reads are exactly the rows it writes, and no other tile touches them.
 //
 // Requirements (checked by the host): periodic box or y walls; nx * sizeof(S)
 // a multiple of 16 (bulk copies move 16-byte multiples between 16-byte-aligned
-// addresses; slot rows start 128-byte aligned); nx <= 2 * 512.
+// addresses; slot rows start 128-byte aligned); nx at most the tile capacity.
 //
-// Every wait is bounded: a stage whose data has not arrived after about a
-// second makes the CTA set bit 2 of the flag, wait (again bounded) for its
-// copies in flight, and return without storing; the host then reports
-// FPCLBM_ERR_TIMEOUT.
+// Every wait is bounded: after about a second a waiting thread sets a shared
+// abort word, which ends every other wait of the CTA at once; the producer
+// then waits (bounded) for its copies in flight, nothing more is stored, and
+// the CTA sets bit 2 of the flag (the host reports FPCLBM_ERR_TIMEOUT).
 #pragma once
 #include "cell.cuh"
 #include "internal.h"
 
 namespace fpc {
-
-constexpr int kStageMaxThreads = 512;
 
 inline StepArgs<f2> pair_args(const StepArgs<float>& a);  // step_kernel.cuh
 constexpr int kStageFlagTimeout = 2;
@@ -115,18 +115,83 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // shared-memory writes of this thread become visible to the bulk copies (async proxy)
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// Pair access to a stage: two values of one slot row at indices i, j (as f2 lanes x, y).
-template <typename S>
-__device__ __forceinline__ f2 stage_ld(const S* row, unsigned i, unsigned j)
+// Shared-memory access by 32-bit shared addresses (explicit ld.shared / st.shared).
+__device__ __forceinline__ uint32_t lds32(uint32_t a)
 {
-    return f2(Store<S>::ld(row + i), Store<S>::ld(row + j));
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(a) : "memory");
+    return v;
 }
-template <typename S>
-__device__ __forceinline__ void stage_st(S* row, unsigned i, unsigned j, f2 v)
+__device__ __forceinline__ uint32_t lds16(uint32_t a)
 {
-    Store<S>::st(row + i, v.v.x);
-    Store<S>::st(row + j, v.v.y);
+    unsigned short v;
+    asm volatile("ld.shared.b16 %0, [%1];\n" : "=h"(v) : "r"(a) : "memory");
+    return v;
 }
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.b32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts16(uint32_t a, unsigned short v)
+{
+    asm volatile("st.shared.b16 [%0], %1;\n" ::"r"(a), "h"(v) : "memory");
+}
+__device__ __forceinline__ f2 lds_f2(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return f2(v);
+}
+__device__ __forceinline__ void sts_f2(uint32_t a, f2 v)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.v.x), "f"(v.v.y) : "memory");
+}
+
+// Values of the storage type in a stage, converted exactly as Store / Store2 do (so the staged
+// kernel stays bit-identical to the paired one): one entry, or two neighbouring entries (4- or
+// 8-byte aligned) as the lanes of an f2.
+template <typename S>
+struct StageIO;
+template <>
+struct StageIO<float> {
+    __device__ __forceinline__ static float ld1(uint32_t a) { return __uint_as_float(lds32(a)); }
+    __device__ __forceinline__ static f2 ld2(uint32_t a) { return lds_f2(a); }
+    __device__ __forceinline__ static void st1(uint32_t a, float v) { sts32(a, __float_as_uint(v)); }
+    __device__ __forceinline__ static void st2(uint32_t a, f2 v) { sts_f2(a, v); }
+};
+template <>
+struct StageIO<__nv_bfloat16> {
+    __device__ __forceinline__ static float ld1(uint32_t a) { return __uint_as_float(lds16(a) << 16); }
+    __device__ __forceinline__ static f2 ld2(uint32_t a)
+    {
+        const uint32_t w = lds32(a);
+        return f2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    __device__ __forceinline__ static void st1(uint32_t a, float v)
+    {
+        sts16(a, __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+    }
+    __device__ __forceinline__ static void st2(uint32_t a, f2 v)
+    {
+        const __nv_bfloat162 b = __float22bfloat162_rn(v.v);
+        sts32(a, *reinterpret_cast<const uint32_t*>(&b));
+    }
+};
+template <>
+struct StageIO<__half> {
+    __device__ __forceinline__ static float ld1(uint32_t a) { return __half2float(__ushort_as_half((unsigned short)lds16(a))); }
+    __device__ __forceinline__ static f2 ld2(uint32_t a)
+    {
+        const uint32_t w = lds32(a);
+        return f2(__half22float2(*reinterpret_cast<const __half2*>(&w)));
+    }
+    __device__ __forceinline__ static void st1(uint32_t a, float v) { sts16(a, __half_as_ushort(__float2half_rn(v))); }
+    __device__ __forceinline__ static void st2(uint32_t a, f2 v)
+    {
+        const __half2 h = __float22half2_rn(v.v);
+        sts32(a, *reinterpret_cast<const uint32_t*>(&h));
+    }
+};
 
 // One bulk copy of `rows` consecutive slot rows between global memory and stage chunk row `lr`.
 struct RowSpan {
@@ -176,202 +241,264 @@ __device__ __forceinline__ int stage_spans(bool store, int s, int y0, int z, int
 // CB: bytes of one slot chunk of a stage (a compile-time constant, so that every shared-memory
 // access of the compute phase is an immediate offset); a tile holds R whole rows, R nx <= CB /
 // sizeof(S).
-template <typename S, bool ODD, int BC, bool FORCE, int MODE, int CB>
-__global__ void __launch_bounds__(kStageMaxThreads) k_step_stage(const StepArgs<f2> a, const FastDiv div_tpp,
-                                                                 const unsigned ntiles, const int ns, const int R)
+// Bounded wait on an mbarrier phase that also gives up when another thread of the CTA has
+// aborted; a wait that runs out (about a second) aborts the CTA.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (global_ns() - t0 > 1000000000ull) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// NCW consumer warps (two cells per thread: tiles of up to 64 NCW cells) and one producer warp;
+// registers capped for 3 resident blocks of 4 consumer warps per SM (one block of 8).
+template <typename S, bool ODD, int BC, bool FORCE, int MODE, int NCW>
+__global__ void __launch_bounds__(32 * (NCW + 1), NCW == 4 ? 3 : 1) k_step_stage(const StepArgs<f2> a, const FastDiv div_tpp,
+                                                               const unsigned ntiles, const int R, const int nsi,
+                                                               const int nso)
 {
     static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y, "periodic box or y walls");
     constexpr bool WALLS = BC == BC_WALLS_Y;
-    constexpr int TC = CB / (int)sizeof(S);  // entries per slot chunk
-    constexpr unsigned stageb = 27u * CB;
+    constexpr unsigned NC = 32 * NCW;            // consumer threads
+    constexpr int TC = 2 * (int)NC;              // entries per slot chunk (cells per tile at most)
+    constexpr unsigned CB = TC * sizeof(S);      // bytes per slot chunk
+    constexpr unsigned STB = 27u * CB;           // bytes per stage
     extern __shared__ __align__(128) unsigned char stage_smem[];
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const unsigned rowb = (unsigned)nx * sizeof(S);
     const unsigned tpp = (unsigned)(ny / R);  // tiles per plane
     const uint32_t sm0 = smem_addr(stage_smem);
-    const uint32_t bar0 = sm0 + (unsigned)ns * stageb;  // ns mbarriers of 8 bytes after the stages
+    const uint32_t in0 = sm0, out0 = sm0 + (unsigned)nsi * STB;
+    const uint32_t bars = out0 + (unsigned)nso * STB;
+    const uint32_t full_in = bars, empty_in = bars + 8u * nsi, full_out = bars + 16u * nsi,
+                   empty_out = bars + 16u * nsi + 8u * nso;
+    volatile int* abort = reinterpret_cast<volatile int*>(stage_smem + (bars - sm0) + 16u * (nsi + nso));
     const unsigned tid = threadIdx.x, lane = tid & 31u;
-    const bool producer = tid < 27;  // lane s of warp 0 moves slot s
     unsigned char* const gbuf = static_cast<unsigned char*>(a.buf);
     const size_t slotb = (size_t)a.stride * sizeof(S);
 
     if (tid == 0) {
-        for (int k = 0; k < ns; ++k) mbar_init(bar0 + 8u * k, 1);
+        for (int k = 0; k < nsi; ++k) {
+            mbar_init(full_in + 8u * k, 1);
+            mbar_init(empty_in + 8u * k, NC);
+        }
+        for (int j = 0; j < nso; ++j) {
+            mbar_init(full_out + 8u * j, NC);
+            mbar_init(empty_out + 8u * j, 1);
+        }
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         fence_proxy_async_smem();
     }
     __syncthreads();
 
-    auto tile_yz = [&](unsigned t, int& y0, int& z) {
-        z = (int)fdiv(t, div_tpp);
-        y0 = (int)(t - (unsigned)z * tpp) * R;
-    };
-    auto gaddr = [&](const RowSpan& q) {
-        return gbuf + (size_t)q.slot * slotb + (size_t)((unsigned)q.y + (unsigned)ny * (unsigned)q.z) * rowb;
-    };
-    // warp 0: lane 0 arms the stage's barrier, lanes 0..26 load their slot's rows
-    auto issue_load = [&](unsigned t, int k) {
-        int y0, z;
-        tile_yz(t, y0, z);
-        const uint32_t bar = bar0 + 8u * k;
-        if (lane == 0) mbar_arrive_expect_tx(bar, 27u * (unsigned)R * rowb);
-        __syncwarp();
-        if (producer) {
-            RowSpan sp[2];
-            const int n = stage_spans<ODD, BC>(false, (int)tid, y0, z, R, ny, nz, sp);
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (q < n)
-                    bulk_load(sm0 + (unsigned)k * stageb + tid * (unsigned)CB + (unsigned)sp[q].lr * rowb, gaddr(sp[q]),
-                              (unsigned)sp[q].rows * rowb, bar);
-        }
-    };
-    auto issue_store = [&](unsigned t, int k) {
-        int y0, z;
-        tile_yz(t, y0, z);
-        if (producer) {
-            RowSpan sp[2];
-            const int n = stage_spans<ODD, BC>(true, (int)tid, y0, z, R, ny, nz, sp);
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (q < n)
-                    bulk_store(gaddr(sp[q]), sm0 + (unsigned)k * stageb + tid * (unsigned)CB + (unsigned)sp[q].lr * rowb,
-                               (unsigned)sp[q].rows * rowb);
-            bulk_commit();
-        }
-    };
+    // this CTA's tiles: t_i = blockIdx.x + i gridDim.x, i < nt
+    const unsigned nt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    // prologue: the first ns - 1 tiles of this CTA in flight
-    unsigned pending = 0;  // stages with loads in flight (warp 0)
-    if (tid < 32)
-        for (int k = 0; k < ns - 1; ++k) {
-            const unsigned t = blockIdx.x + (unsigned)k * gridDim.x;
-            if (t < ntiles) {
-                issue_load(t, k);
-                pending |= 1u << k;
+    if (tid >= NC) {  // ---------------- producer warp ----------------
+        const bool mover = lane < 27;  // lane s moves slot s
+        auto tile_yz = [&](unsigned i, int& y0, int& z) {
+            const unsigned t = blockIdx.x + i * gridDim.x;
+            z = (int)fdiv(t, div_tpp);
+            y0 = (int)(t - (unsigned)z * tpp) * R;
+        };
+        auto gaddr = [&](const RowSpan& q) {
+            return gbuf + (size_t)q.slot * slotb + (size_t)((unsigned)q.y + (unsigned)ny * (unsigned)q.z) * rowb;
+        };
+        auto issue_load = [&](unsigned i, int k) {
+            int y0, z;
+            tile_yz(i, y0, z);
+            const uint32_t bar = full_in + 8u * k;
+            if (lane == 0) mbar_arrive_expect_tx(bar, 27u * (unsigned)R * rowb);
+            __syncwarp();
+            if (mover) {
+                RowSpan sp[2];
+                const int n = stage_spans<ODD, BC>(false, (int)lane, y0, z, R, ny, nz, sp);
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (q < n)
+                        bulk_load(in0 + (unsigned)k * STB + lane * CB + (unsigned)sp[q].lr * rowb, gaddr(sp[q]),
+                                  (unsigned)sp[q].rows * rowb, bar);
             }
+        };
+        auto issue_store = [&](unsigned i, int j) {
+            int y0, z;
+            tile_yz(i, y0, z);
+            if (mover) {
+                RowSpan sp[2];
+                const int n = stage_spans<ODD, BC>(true, (int)lane, y0, z, R, ny, nz, sp);
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (q < n)
+                        bulk_store(gaddr(sp[q]), out0 + (unsigned)j * STB + lane * CB + (unsigned)sp[q].lr * rowb,
+                                   (unsigned)sp[q].rows * rowb);
+                bulk_commit();
+            }
+        };
+        unsigned lastpar = 0;  // bit k: parity of the phase of the last load issued into input stage k
+        unsigned issued = 0;   // bit k: input stage k has received a load
+        const unsigned pro = nt < (unsigned)nsi ? nt : (unsigned)nsi;
+        for (unsigned k = 0; k < pro; ++k) {
+            issue_load(k, (int)k);
+            issued |= 1u << k;
         }
+        bool ok = true;
+        int ki = 0, ko = 0;
+        for (unsigned i = 0; i < nt; ++i) {
+            // refill input stage ki with tile i + nsi once the consumers have read tile i from it
+            if (i + nsi < nt) {
+                ok = mbar_wait_or_abort(empty_in + 8u * ki, (i / nsi) & 1u, abort);
+                if (!ok) break;
+                issue_load(i + nsi, ki);
+                lastpar ^= 1u << ki;
+            }
+            // store tile i once the consumers have written it
+            ok = mbar_wait_or_abort(full_out + 8u * ko, (i / nso) & 1u, abort);
+            if (!ok) break;
+            issue_store(i, ko);
+            // the previous tile's output stage is free once its store has read it
+            if (i >= 1) {
+                if (mover) bulk_wait_read_all_but_last();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty_out + 8u * (ko == 0 ? nso - 1 : ko - 1));
+            }
+            ki = ki + 1 == nsi ? 0 : ki + 1;
+            ko = ko + 1 == nso ? 0 : ko + 1;
+        }
+        if (!ok && lane == 0) {
+            atomicOr(a.flag, kStageFlagTimeout);
+            // let the loads still in flight land before the CTA's shared memory is released
+            for (int k = 0; k < nsi; ++k)
+                if (issued & (1u << k)) mbar_wait_bounded(full_in + 8u * k, (lastpar >> k) & 1u);
+        }
+        if (mover) bulk_wait_all();
+        return;
+    }
 
-    // this thread's cells x, x + 1 of local row r and their wrapped neighbours in the row
+    // ---------------- consumer warps: cells x, x + 1 of local row r ----------------
     const unsigned half = (unsigned)nx / 2;
     const unsigned r = tid / half, x = 2u * (tid - r * half);
     const bool act = r < (unsigned)R;
     const unsigned rb = r * (unsigned)nx;
-    const unsigned ia = rb + x;                                    // the cells' own entries
+    const unsigned ia = rb + x;                                     // the cells' own entries
     const unsigned im1 = rb + (x == 0 ? (unsigned)nx - 1 : x - 1);  // x - 1 of the first cell
     const unsigned ip2 = rb + (x + 2 == (unsigned)nx ? 0u : x + 2); // x + 1 of the second cell
     const Rates<f2>& rt = a.rates;
-    unsigned parity = 0;  // bit k: phase parity of stage k's next completion
-    bool timed_out = false;
-    int k = 0;
-    for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const bool ok = mbar_wait_bounded(bar0 + 8u * k, (parity >> k) & 1u);
-        S* const st = reinterpret_cast<S*>(stage_smem + (size_t)k * stageb);
+    int ki = 0, ko = 0;
+    for (unsigned i = 0; i < nt; ++i) {
+        if (!mbar_wait_or_abort(full_in + 8u * ki, (i / nsi) & 1u, abort)) return;
         bool top = false, bot = false;  // this thread's row touches the wall y = ny - 1/2 / y = -1/2
         if (WALLS) {
+            const unsigned t = blockIdx.x + i * gridDim.x;
             const unsigned y = (t - fdiv(t, div_tpp) * tpp) * (unsigned)R + r;
             bot = y == 0;
             top = y + 1 == (unsigned)ny;
         }
+        // byte addresses in this input stage of the cells' own entries and of their x neighbours
+        constexpr unsigned ES = sizeof(S);
+        const uint32_t ain = in0 + (unsigned)ki * STB;
+        const uint32_t pa = ain + ES * ia, pm1 = ain + ES * im1, pp2 = ain + ES * ip2;
         f2 g[27];
-        if (ok && act) {
+        if (act) {
 #pragma unroll
             for (int s = 0; s < 27; ++s) {
-                const S* row = st + s * TC;
+                const unsigned so = (unsigned)s * CB;  // slot chunk offset (compile-time)
                 const int ix = s % 3, iy = (s / 3) % 3;
                 // the value streaming in for slot s comes from x - e_x (e_x = ix - 1); a source in the
                 // wall is the cell's own reflected value (no shift)
                 const bool wall = WALLS && ((iy == 2 && bot) || (iy == 0 && top));
                 if (!ODD || ix == 1) {
-                    g[s] = Store2<S>::ld(row + ia);
+                    g[s] = StageIO<S>::ld2(pa + so);
                 } else if (ix == 0) {  // e_x = -1: sources x + 1, x + 2
-                    g[s] = wall ? Store2<S>::ld(row + ia) : stage_ld(row, ia + 1, ip2);
+                    g[s] = wall ? StageIO<S>::ld2(pa + so)
+                                : f2(StageIO<S>::ld1(pa + so + ES), StageIO<S>::ld1(pp2 + so));
                 } else {  // e_x = +1: sources x - 1, x
-                    g[s] = wall ? Store2<S>::ld(row + ia) : stage_ld(row, im1, ia);
+                    g[s] = wall ? StageIO<S>::ld2(pa + so)
+                                : f2(StageIO<S>::ld1(pm1 + so), StageIO<S>::ld1(pa + so));
                 }
             }
         }
-        // odd step: a thread's writes land on its neighbours' read positions
-        if (ODD) __syncthreads();
-        if (ok && act) {
-            const bool fine = collide_cell<f2, FORCE, MODE>(g, rt, a.Fx, a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6],
-                                                            rt.om[8], rt.om[9], nullptr);
-            if (!fine) atomicOr(a.flag, 1);
+        mbar_arrive(empty_in + 8u * ki);
+        bool fine = true;
+        if (act)
+            fine = collide_cell<f2, FORCE, MODE>(g, rt, a.Fx, a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6], rt.om[8],
+                                                 rt.om[9], nullptr);
+        if (!fine) atomicOr(a.flag, 1);
+        if (i >= (unsigned)nso && !mbar_wait_or_abort(empty_out + 8u * ko, ((i / nso) - 1u) & 1u, abort)) return;
+        const uint32_t aout = out0 + (unsigned)ko * STB;
+        const uint32_t qa = aout + ES * ia, qm1 = aout + ES * im1, qp2 = aout + ES * ip2;
+        if (act) {
 #pragma unroll
             for (int s = 0; s < 27; ++s) {
-                S* row = st + s * TC;
+                const unsigned so = (unsigned)s * CB;
                 const int ix = s % 3, iy = (s / 3) % 3;
                 // destination x + e_x; a link into the wall stays at the cell (reflected)
                 const bool wall = WALLS && ((iy == 0 && bot) || (iy == 2 && top));
                 if (!ODD || ix == 1) {
-                    Store2<S>::st(row + ia, g[s]);
+                    StageIO<S>::st2(qa + so, g[s]);
                 } else if (ix == 2) {  // e_x = +1: destinations x + 1, x + 2
-                    if (wall) Store2<S>::st(row + ia, g[s]);
-                    else stage_st(row, ia + 1, ip2, g[s]);
+                    if (wall) {
+                        StageIO<S>::st2(qa + so, g[s]);
+                    } else {
+                        StageIO<S>::st1(qa + so + ES, g[s].v.x);
+                        StageIO<S>::st1(qp2 + so, g[s].v.y);
+                    }
                 } else {  // e_x = -1: destinations x - 1, x
-                    if (wall) Store2<S>::st(row + ia, g[s]);
-                    else stage_st(row, im1, ia, g[s]);
+                    if (wall) {
+                        StageIO<S>::st2(qa + so, g[s]);
+                    } else {
+                        StageIO<S>::st1(qm1 + so, g[s].v.x);
+                        StageIO<S>::st1(qa + so, g[s].v.y);
+                    }
                 }
             }
         }
         fence_proxy_async_smem();
-        if (__syncthreads_or(!ok)) {  // some thread's stage never arrived: stop, store nothing
-            timed_out = true;
-            break;
-        }
-        parity ^= 1u << k;
-        if (tid < 32) {
-            pending &= ~(1u << k);
-            issue_store(t, k);
-            // the stage of the previous tile is free once its store has read it (each lane waits
-            // for its own slot's store): refill it with the tile ns - 1 ahead of this one
-            const int kp = k == 0 ? ns - 1 : k - 1;
-            const unsigned tn = t + (unsigned)(ns - 1) * gridDim.x;
-            if (tn < ntiles) {
-                if (producer) bulk_wait_read_all_but_last();
-                issue_load(tn, kp);
-                pending |= 1u << kp;
-            }
-        }
-        k = k + 1 == ns ? 0 : k + 1;
-    }
-    if (tid < 32) {
-        if (timed_out && tid == 0) {
-            atomicOr(a.flag, kStageFlagTimeout);
-            // let the copies still in flight land before the CTA's shared memory is released
-            for (int q = 0; q < ns; ++q)
-                if (pending & (1u << q)) mbar_wait_bounded(bar0 + 8u * q, (parity >> q) & 1u);
-        }
-        if (producer) bulk_wait_all();
+        mbar_arrive(full_out + 8u * ko);
+        ki = ki + 1 == nsi ? 0 : ki + 1;
+        ko = ko + 1 == nso ? 0 : ko + 1;
     }
 }
 
-// Rows per tile: the largest R with R nx <= entries of a chunk that divides ny (1 if none).
-inline int stage_rows(int nx, int ny, int chunk_entries)
+// Rows per tile: the largest R with R nx <= the tile capacity that divides ny (1 if none).
+inline int stage_rows(int nx, int ny, int cap)
 {
-    for (int R = chunk_entries / nx; R > 1; --R)
+    for (int R = cap / nx; R > 1; --R)
         if (ny % R == 0) return R;
     return 1;
 }
 
-// Launch: one CTA per resident slot (persistent), R nx / 2 threads rounded up to a warp, ns stages.
-template <typename S, bool ODD, int BC, bool FORCE, int MODE, int CB>
-cudaError_t step_go_stage_cb(const StepArgs<float>& a, int ns, cudaStream_t st)
+// Launch: one CTA per resident slot (persistent); nsi input and nso = 2 output stages.
+template <typename S, bool ODD, int BC, bool FORCE, int MODE, int NCW>
+cudaError_t step_go_stage_ncw(const StepArgs<float>& a, int nsi, cudaStream_t st)
 {
-    constexpr int TC = CB / (int)sizeof(S);
+    constexpr int TC = 64 * NCW;
+    constexpr int nso = 2;
     const int R = stage_rows(a.nx, a.ny, TC);
-    const int threads = (R * a.nx / 2 + 31) / 32 * 32;
-    const size_t smem = (size_t)ns * 27 * CB + 8 * (size_t)ns;
-    auto kern = k_step_stage<S, ODD, BC, FORCE, MODE, CB>;
-    // resident blocks per SM for the last (threads, shared memory) this instantiation launched with,
+    const int threads = 32 * (NCW + 1);
+    const size_t smem = (size_t)(nsi + nso) * 27 * TC * sizeof(S) + 16 * (size_t)(nsi + nso) + 16;
+    auto kern = k_step_stage<S, ODD, BC, FORCE, MODE, NCW>;
+    // resident blocks per SM for the last shared-memory size this instantiation launched with,
     // on the device of that launch (a benign race: every thread computes the same values)
-    static int c_dev = -1, c_threads = 0, c_per_sm = 0, c_sms = 0;
+    static int c_dev = -1, c_per_sm = 0, c_sms = 0;
     static size_t c_smem = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    if (dev == c_dev && threads == c_threads && smem == c_smem) {
+    if (dev == c_dev && smem == c_smem) {
         per_sm = c_per_sm;
         sms = c_sms;
     } else {
@@ -386,25 +513,24 @@ cudaError_t step_go_stage_cb(const StepArgs<float>& a, int ns, cudaStream_t st)
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         c_per_sm = per_sm;
         c_sms = sms;
-        c_threads = threads;
         c_smem = smem;
         c_dev = dev;
     }
     const unsigned ntiles = (unsigned)(a.ny / R) * (unsigned)a.nz;
     unsigned grid = (unsigned)(per_sm * sms);
     if (grid > ntiles) grid = ntiles;
-    kern<<<grid, threads, smem, st>>>(pair_args(a), make_fastdiv((unsigned)(a.ny / R)), ntiles, ns, R);
+    kern<<<grid, threads, smem, st>>>(pair_args(a), make_fastdiv((unsigned)(a.ny / R)), ntiles, R, nsi, nso);
     return cudaGetLastError();
 }
 
-// Chunks of 1 KB (rows up to 1 KB: 512 cells of 16-bit storage, 256 of fp32) or 2 KB.
+// Tiles of up to 256 cells (4 consumer warps) for rows of at most 256 cells, else up to 512
+// (8 consumer warps).
 template <typename S, bool ODD, int BC, bool FORCE, int MODE>
-cudaError_t step_go_stage(const StepArgs<float>& a, int ns, cudaStream_t st)
+cudaError_t step_go_stage(const StepArgs<float>& a, int nsi, cudaStream_t st)
 {
-    const size_t rowb = (size_t)a.nx * sizeof(S);
-    if (rowb % 16 != 0 || rowb > 2048 || a.nx < 2 || ns < 3 || ns > 8) return cudaErrorInvalidValue;
-    if (rowb <= 1024) return step_go_stage_cb<S, ODD, BC, FORCE, MODE, 1024>(a, ns, st);
-    return step_go_stage_cb<S, ODD, BC, FORCE, MODE, 2048>(a, ns, st);
+    if ((a.nx * sizeof(S)) % 16 != 0 || a.nx > 512 || a.nx < 2 || nsi < 2 || nsi > 6) return cudaErrorInvalidValue;
+    if (a.nx <= 256) return step_go_stage_ncw<S, ODD, BC, FORCE, MODE, 4>(a, nsi, st);
+    return step_go_stage_ncw<S, ODD, BC, FORCE, MODE, 8>(a, nsi, st);
 }
 
 }  // namespace fpc

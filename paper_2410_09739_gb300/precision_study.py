@@ -8,11 +8,12 @@ parity (per-step relative difference below 1e-12), so these are errors of the re
 
 Workloads (the performance configurations of the paper's test cases, Sec. 4):
   tgv      Taylor-Green vortex, Re = 1600, 256^3 periodic, U = u0 = 0.05
+  tgv512   the same on 512^3 (viscosity from Re at that size)
   channel  walls in y, body force, Re_tau = 180, 384 x 192 x 192, U = bulk velocity 16 u*
   cavity   lid-driven cubic cavity, Re = 1000, Ma = 0.1, 150^3, U = lid velocity
   shear2d  D2Q9 doubly periodic shear layers, Re = 30000, Ma = 0.2, 4096^2, U = layer velocity
 
-Usage: python -m paper_2410_09739_gb300.precision_study [--steps 1000] [--workloads tgv channel ...]
+Usage: python -m paper_2410_09739_gb300.precision_study [--steps 1000] [--workloads tgv tgv512 channel ...]
 Prints one JSON object.
 """
 from __future__ import annotations
@@ -38,8 +39,8 @@ PRECISIONS = ("fp64", "fp32", "fp16", "bf16")
 
 def workload(name):
     """(make(prec) -> lattice with fields set, velocity scale U, description)."""
-    if name == "tgv":
-        n, u0 = 256, 0.05
+    if name in ("tgv", "tgv512"):
+        n, u0 = (256 if name == "tgv" else 512), 0.05
         tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
         flds = W.tgv(n, u0)
 
@@ -48,7 +49,7 @@ def workload(name):
             lat.set_params(tau)
             lat.init_fields(*flds)
             return lat
-        return make, u0, "TGV Re=1600 256^3, u0=0.05, tau=%.6f" % tau
+        return make, u0, "TGV Re=1600 %d^3, u0=0.05, tau=%.6f" % (n, tau)
     if name == "channel":
         nx, ny, nz, us = 384, 192, 192, 0.005
         H = ny / 2
@@ -88,7 +89,16 @@ def workload(name):
     raise ValueError("unknown workload %r" % name)
 
 
+def device_moments(lat, torch):
+    """rho, u of every cell as device tensors (fpclbm_moments / fpclbm2d_moments on the device)."""
+    nf = 3 if isinstance(lat, F.Lattice2D) else 4
+    outs = [torch.empty(lat.ncells, dtype=torch.float64, device="cuda") for _ in range(nf)]
+    (F.fpclbm2d_moments if nf == 3 else F.fpclbm_moments)(lat.h, *outs, on_device=1)
+    return outs
+
+
 def run(name, steps):
+    import torch
     make, U, desc = workload(name)
     ref = None
     out = {"workload": name, "description": desc, "steps": steps, "U": U}
@@ -96,27 +106,29 @@ def run(name, steps):
         t0 = time.perf_counter()
         with make(prec) as lat:
             lat.step(steps)
-            m = lat.moments()
+            m = device_moments(lat, torch)
+        torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         rho, vel = m[0], m[1:]
-        if ref is None:
-            ref = (float(np.sum(rho)), vel)
+        if ref is None:  # the FP64 run, kept on the device
+            ref = (float(torch.sum(rho)), vel)
             out["fp64_seconds"] = secs
             continue
         d = [v - r for v, r in zip(vel, ref[1])]
-        finite = all(np.all(np.isfinite(x)) for x in d)
-        mx = max(float(np.max(np.abs(x))) for x in d) / U if finite else float("inf")
-        rms = math.sqrt(sum(float(np.mean(x * x)) for x in d) / len(d)) / U if finite else float("inf")
+        finite = all(bool(torch.isfinite(x).all()) for x in d)
+        mx = max(float(torch.max(torch.abs(x))) for x in d) / U if finite else float("inf")
+        rms = math.sqrt(sum(float(torch.mean(x * x)) for x in d) / len(d)) / U if finite else float("inf")
         out[prec] = {"max_du_over_U": mx, "rms_du_over_U": rms,
-                     "mass_rel": float(abs(np.sum(rho) - ref[0]) / ref[0]), "seconds": secs}
+                     "mass_rel": float(abs(float(torch.sum(rho)) - ref[0]) / ref[0]), "seconds": secs}
         print("%s %s: max %.3e rms %.3e" % (name, prec, mx, rms), file=sys.stderr, flush=True)
+        del rho, vel, d, m
     return out
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--workloads", nargs="+", default=["tgv", "channel", "cavity", "shear2d"])
+    ap.add_argument("--workloads", nargs="+", default=["tgv", "tgv512", "channel", "cavity", "shear2d"])
     args = ap.parse_args(argv)
     t0 = time.perf_counter()
     res = [run(w, args.steps) for w in args.workloads]

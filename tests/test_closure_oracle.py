@@ -97,3 +97,19 @@ def test_eddy_viscosity_recovers_a_planted_nu_t():
         nut = C.eddy_viscosity(u, uu, walls_y=False)
         mask = sum(S[i][j] ** 2 for i in range(3) for j in range(3)) > 1e-14
         assert np.allclose(nut[mask], expect, rtol=1e-10, atol=1e-15)
+
+
+def test_wall_derivative_is_exact_for_quadratics_vanishing_at_the_walls():
+    """Filtered velocity between no-slip walls at y = -1/2 and cy - 1/2: the derivative at every
+    row, the first and last included, is exact for (y + 1/2)(cy - 1/2 - y) and for profiles
+    linear near one wall; a first-order one-sided difference at the end rows is not."""
+    cy = 6
+    y = np.arange(cy, dtype=float)
+    for prof, dprof in (((y + 0.5) * (cy - 0.5 - y), (cy - 0.5 - y) - (y + 0.5)),):
+        g = np.broadcast_to(prof[None, :, None], (2, cy, 3)).copy()
+        d = C.wall_ddy(g)
+        assert np.allclose(d, np.broadcast_to(dprof[None, :, None], g.shape), rtol=0, atol=1e-13)
+        one_sided = g[:, 1, :] - g[:, 0, :]
+        assert np.max(np.abs(one_sided - dprof[0])) > 0.1
+    lin = np.broadcast_to((y + 0.5)[None, :, None], (2, cy, 3))  # vanishes at y = -1/2
+    assert np.allclose(C.wall_ddy(lin)[:, :-1, :], 1.0, rtol=0, atol=1e-13)

@@ -141,8 +141,8 @@ def _mlp_bf16_operands(theta, x):
 
 def _learned_step_oracle(f0, theta, omega_base, bc=0):
     """One step of the learned-mode collision with the oracle: per cell, delta omega from the MLP
-    on (kappa_2 - kappa_2^Mv, u), added to the shear rates (clamped to [0.02, 1.98]), then collide and
-    push-stream."""
+    on (kappa_2 - kappa_2^Mv, u); the shear rates become max(omega + min(delta omega, 0), 0.02) (the
+    correction only adds viscosity, as its training labels do); then collide and push-stream."""
     _, nz, ny, nx = f0.shape
     e = O.velocity_set()
     mnp = [tuple(v) for v in O.moment_exponents()]
@@ -160,7 +160,7 @@ def _learned_step_oracle(f0, theta, omega_base, bc=0):
                 dw = _mlp_bf16_operands(theta, feat)
                 om = omega_base.copy()
                 for j in (4, 5, 6, 8, 9):
-                    om[j] = min(max(om[j] + dw, 0.02), 1.98)
+                    om[j] = max(om[j] + min(dw, 0.0), 0.02)
                 ft = O.collide(f, (0, 0, 0), om, O.EQ_MODE_FP)
                 for a in range(27):
                     out[a, (z + e[a, 2]) % nz, (y + e[a, 1]) % ny, (x + e[a, 0]) % nx] = ft[a]

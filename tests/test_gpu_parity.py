@@ -455,7 +455,8 @@ def test_velocity_error_after_1000_steps():
     """Stated bound: FP32 path within 1e-5 (relative to u0) in velocity after 1000 steps of the
     256^3 Re = 1600 TGV, against the FP64 GPU path (itself at oracle parity).  The 16-bit storage
     variants have no stated bound; their errors are measured and printed (max and RMS of |du|/u0)
-    and checked only against loose ceilings (FP16 5e-2, BF16 2.5e-1) that catch a broken path."""
+    and checked against about twice the values the storage-precision study measured on this
+    workload (FP16 max 1.17e-2 / RMS 1.53e-3, BF16 9.49e-2 / 2.24e-2), so a regression of 2x fails."""
     torch = pytest.importorskip("torch")
     n, u0, steps = 256, 0.05, 1000
     nu = W.tgv_viscosity(n, u0, 1600.0)
@@ -477,5 +478,5 @@ def test_velocity_error_after_1000_steps():
         errs[prec] = (mx, rms)
         print("%s storage, max |du|/u0 after %d steps: %.3e (rms %.3e)" % (prec, steps, mx, rms))
     assert errs["fp32"][0] <= 1e-5
-    assert errs["fp16"][0] <= 5e-2
-    assert errs["bf16"][0] <= 2.5e-1
+    assert errs["fp16"][0] <= 2.4e-2 and errs["fp16"][1] <= 3.1e-3
+    assert errs["bf16"][0] <= 1.9e-1 and errs["bf16"][1] <= 4.5e-2
