@@ -103,7 +103,8 @@ def peaks():
         return 6800.0, "fallback"
 
 
-STEP_KERNEL_SOURCES = ("common.cuh", "collide.cuh", "pair.cuh", "closure.cuh", "cell.cuh", "step_kernel.cuh", "step_fp32.cu",
+STEP_KERNEL_SOURCES = ("common.cuh", "collide.cuh", "pair.cuh", "closure.cuh", "cell.cuh", "step_kernel.cuh", "stage.cuh",
+                       "step_fp32.cu",
                        "step_fp32_odd.cu", "step_fp16.cu", "step_fp16_odd.cu", "step_bf16.cu", "step_bf16_odd.cu",
                        "step_fp64.cu", "step_kernels.cu", "internal.h")
 

@@ -20,7 +20,12 @@ With --windows K the fine run continues through K successive collection windows 
 spin-up, each with its own training and coarse runs: K independent estimates of the errors and
 their spread from one spin-up.
 
+With --flow tgv the same pipeline runs on decaying turbulence instead: the Taylor-Green vortex in a
+periodic box, fine n^3 against (n/r)^3, comparing the coarse runs' kinetic energy with the filtered
+fine kinetic energy over time (decay() below).
+
 Usage: python -m paper_2410_09739_gb300.closure_study [--fine 384 192 192] [--r 4] [--windows 2] ...
+       python -m paper_2410_09739_gb300.closure_study --flow tgv --fine 256 256 256 --r 2
 Prints one JSON object (progress on stderr).
 """
 from __future__ import annotations
@@ -56,6 +61,13 @@ def parse(argv=None):
     p.add_argument("--precision", default="bf16")
     p.add_argument("--seed", type=int, default=7)
     p.add_argument("--cs", type=float, default=0.1, help="Smagorinsky constant of the non-learned baseline")
+    p.add_argument("--out", default=None, help="also write the JSON result to this file (after every window)")
+    p.add_argument("--flow", default="channel", choices=["channel", "tgv"],
+                   help="channel (walls, body force, mean profile) or tgv (decaying Taylor-Green vortex in a "
+                        "periodic box, kinetic-energy history)")
+    p.add_argument("--re", type=float, default=1600.0, help="tgv: Reynolds number u0 L / nu, L = n / (2 pi)")
+    p.add_argument("--t-end", type=float, default=15.0, help="tgv: convective times L / u0")
+    p.add_argument("--dt", type=float, default=0.5, help="tgv: convective times between snapshots")
     p.add_argument("--windows", type=int, default=1,
                    help="successive collection windows of the same fine run, each with its own training and "
                         "coarse runs (run-to-run spread)")
@@ -234,7 +246,12 @@ def run(args):
     out["spinup_seconds"] = time.perf_counter() - t0
 
     # successive windows of the same fine run: one training and one set of coarse runs each
-    wins = [window(fine, args, geo, args.seed + k) for k in range(args.windows)]
+    wins = []
+    for k in range(args.windows):
+        wins.append(window(fine, args, geo, args.seed + k))
+        if args.out:  # partial result after every window
+            with open(args.out, "w") as fh:
+                json.dump(dict(out, windows=wins, partial=k + 1 < args.windows), fh)
     fine.close()
     out["windows"] = wins
     # the first window under the keys of a single-window study
@@ -254,9 +271,99 @@ def run(args):
     return out
 
 
+def decay(args):
+    """Decaying turbulence: the Taylor-Green vortex at Reynolds number args.re in a periodic box,
+    fine n^3 and coarse (n/r)^3 (acoustic scaling: the same Re on both grids).  The fine run is
+    box-filtered every args.dt convective times (features, labels, filtered kinetic energy), the
+    network is trained on all snapshots, and coarse runs from the filtered initial field (plain,
+    learned, Smagorinsky without wall damping) record their kinetic energy at the same times.
+    Error of a coarse run: RMS over the snapshots of KE_coarse / KE_filtered - 1."""
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    nf, r, u0 = args.fine[0], args.r, 0.05
+    n = nf // r
+    nu_f = W.tgv_viscosity(nf, u0, args.re)
+    tau_f, tau_c = 3.0 * nu_f + 0.5, 3.0 * nu_f / r + 0.5
+    Tc = (n / (2.0 * math.pi)) / u0  # coarse steps per convective time
+    per_c = max(1, int(round(args.dt * Tc)))
+    n_snap = int(round(args.t_end / args.dt)) + 1
+    nc = n ** 3
+    out = {"config": {"flow": "tgv", "fine": nf, "coarse": n, "r": r, "re": args.re, "u0": u0, "tau_fine": tau_f,
+                      "tau_coarse": tau_c, "t_end": args.t_end, "dt": args.dt, "coarse_steps_per_snapshot": per_c,
+                      "precision": args.precision, "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
+                      "seed": args.seed, "cs": args.cs}}
+    fine = F.Lattice(nf, nf, nf, args.precision, stream=stream)
+    fine.set_params(tau_f)
+    fine.init_fields(*W.tgv(nf, u0))
+    X = torch.empty((n_snap * nc, 9), dtype=torch.float32, device="cuda")
+    T = torch.empty(n_snap * nc, dtype=torch.float32, device="cuda")
+    ke_f = []
+    t0 = time.perf_counter()
+    for k in range(n_snap):
+        F.fpclbm_closure_sample(fine.h, r, tau_c, X[k * nc:(k + 1) * nc], T[k * nc:(k + 1) * nc], on_device=1)
+        u = X[k * nc:(k + 1) * nc, 6:9].double()
+        ke_f.append(0.5 * float((u * u).sum(dim=1).mean()))
+        if k < n_snap - 1:
+            fine.step(r * per_c)
+    fine.close()
+    fine_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    w, losses = F.fpclbm_closure_train(X, T, n_snap * nc, args.epochs, args.batch, args.lr, seed=args.seed,
+                                       stream=stream)
+    labels = T.cpu().numpy()
+    out["training"] = {"samples": n_snap * nc, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                       "seconds": time.perf_counter() - t0, "label_mean": float(labels.mean()),
+                       "label_min": float(labels.min())}
+    u0c = X[:nc, 6:9].double().cpu().numpy()
+    del X, T
+    fields = (np.ones(nc), np.ascontiguousarray(u0c[:, 0]), np.ascontiguousarray(u0c[:, 1]),
+              np.ascontiguousarray(u0c[:, 2]))
+    buf = [torch.empty(nc, dtype=torch.float64, device="cuda") for _ in range(4)]
+    kef = np.array(ke_f)
+    runs = {}
+    for name in ("plain", "learned", "smagorinsky"):
+        lat = F.Lattice(n, n, n, args.precision, stream=stream)
+        if name == "learned":
+            lat.set_closure(w)
+            lat.set_params(tau_c, 0.0, F.FPCLBM_DIFF_FP_LEARNED)
+        elif name == "smagorinsky":  # no walls: no van Driest damping
+            lat.set_params(tau_c, 0.0, F.FPCLBM_DIFF_FP_SMAGORINSKY)
+            lat.set_smagorinsky(args.cs, 0.0, 0.0)
+        else:
+            lat.set_params(tau_c)
+        lat.init_fields(*fields)
+        ke, status, secs = [], "ok", 0.0
+        try:
+            for k in range(n_snap):
+                F.fpclbm_moments(lat.h, *buf, on_device=1)
+                ke.append(0.5 * float((buf[1] ** 2 + buf[2] ** 2 + buf[3] ** 2).mean()))
+                if k < n_snap - 1:
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    lat.step(per_c)
+                    secs += time.perf_counter() - t1
+        except F.FpclbmError as e:
+            status = "diverged at snapshot %d (%s)" % (len(ke), e)
+        lat.close()
+        kc = np.array(ke)
+        err = float(np.sqrt(np.mean((kc / kef[:len(kc)] - 1.0) ** 2))) if status == "ok" else None
+        runs[name] = {"status": status, "ke_rel_rms_error": err, "seconds": secs,
+                      "ke_over_ke0": [float(v / ke_f[0]) for v in ke]}
+    out["ke_fine_over_ke0"] = [float(v / ke_f[0]) for v in ke_f]
+    out["coarse"] = runs
+    out["fine_seconds"] = fine_s
+    out["errors"] = {k: v["ke_rel_rms_error"] for k, v in runs.items()}
+    return out
+
+
 def main(argv=None):
     args = parse(argv)
-    print(json.dumps(run(args)))
+    res = decay(args) if args.flow == "tgv" else run(args)
+    if args.out:
+        with open(args.out, "w") as fh:
+            json.dump(res, fh)
+    print(json.dumps(res))
 
 
 if __name__ == "__main__":

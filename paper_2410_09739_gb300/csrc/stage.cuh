@@ -262,10 +262,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
-// NCW consumer warps (two cells per thread: tiles of up to 64 NCW cells) and one producer warp;
-// registers capped for 3 resident blocks of 4 consumer warps per SM (one block of 8).
+// Resident blocks per SM the registers are capped for: four blocks of 4 consumer warps (96
+// registers) for the unit-rate collision without force, which fits them without spilling, three
+// for the other modes, one block of 8 consumer warps.
+__host__ __device__ constexpr int stage_min_blocks(int NCW, bool FORCE, int MODE)
+{
+    return NCW != 4 ? 1 : (r1_mode(MODE) && !FORCE) ? 4 : 3;
+}
+
+// NCW consumer warps (two cells per thread: tiles of up to 64 NCW cells) and one producer warp.
 template <typename S, bool ODD, int BC, bool FORCE, int MODE, int NCW>
-__global__ void __launch_bounds__(32 * (NCW + 1), NCW == 4 ? 3 : 1) k_step_stage(const StepArgs<f2> a, const FastDiv div_tpp,
+__global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, MODE)) k_step_stage(const StepArgs<f2> a, const FastDiv div_tpp,
                                                                const unsigned ntiles, const int R, const int nsi,
                                                                const int nso)
 {
