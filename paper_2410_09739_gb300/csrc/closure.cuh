@@ -42,6 +42,7 @@ __device__ __forceinline__ float tanh_mufu(float x)
     return y;
 }
 
+// D += A B (bf16 x bf16 -> fp32, accumulator in place)
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                                uint32_t b0, uint32_t b1)
 {
@@ -52,7 +53,26 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint3
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// delta omega of this lane's cell from its 9 inputs (warp-collective).
+// D = A B + C with the accumulator input C given separately (a bias row), so no register copy of
+// it is needed before the product.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint2 b, float c0, float c1,
+                                               float c2, float c3)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%12,%13};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
+}
+
+// Two consecutive words of the packed closure (every pair read here starts at an even word of a
+// cudaMalloc'd array, so one 8-byte load).
+__device__ __forceinline__ uint2 ldg_pair(const uint32_t* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
+__device__ __forceinline__ float2 ldg_pair(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+
+// delta omega of this lane's cell from its 9 inputs (warp-collective).  The warp's 32 cells form
+// two 16-row tiles; every weight fragment and bias pair is loaded once and used by both tiles, and
+// the biases enter each product as its accumulator input.
 template <typename R>
 __device__ R closure_delta_omega(const uint32_t* __restrict__ P, const R in[9])
 {
@@ -66,10 +86,11 @@ __device__ R closure_delta_omega(const uint32_t* __restrict__ P, const R in[9])
     q[2] = pack_bf16x2((float)in[4], (float)in[5]);
     q[3] = pack_bf16x2((float)in[6], (float)in[7]);
     q[4] = pack_bf16x2((float)in[8], 0.f);
-    float mine = 0.f;
+    // layer-1 A fragments of tile mt: rows g and g+8 (cells 16 mt + g, 16 mt + g + 8), K columns
+    // 2t, 2t+1 (and + 8: only input 8 and zeros)
+    uint32_t a1[2][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-        // layer-1 A fragments: rows g and g+8 of this 16-cell tile, K columns 2t, 2t+1 (and +8)
         const unsigned rlo = 16u * mt + g, rhi = rlo + 8u;
         uint32_t plo[5], phi[5];
 #pragma unroll
@@ -77,53 +98,63 @@ __device__ R closure_delta_omega(const uint32_t* __restrict__ P, const R in[9])
             plo[k] = __shfl_sync(0xffffffffu, q[k], rlo);
             phi[k] = __shfl_sync(0xffffffffu, q[k], rhi);
         }
-        const uint32_t a0 = t == 0 ? plo[0] : t == 1 ? plo[1] : t == 2 ? plo[2] : plo[3];
-        const uint32_t a1 = t == 0 ? phi[0] : t == 1 ? phi[1] : t == 2 ? phi[2] : phi[3];
-        const uint32_t a2 = t == 0 ? plo[4] : 0u;
-        const uint32_t a3 = t == 0 ? phi[4] : 0u;
-        // layer 1 + tanh, re-packed as the layer-2 A fragments
-        uint32_t A2[4][4];
+        a1[mt][0] = t == 0 ? plo[0] : t == 1 ? plo[1] : t == 2 ? plo[2] : plo[3];
+        a1[mt][1] = t == 0 ? phi[0] : t == 1 ? phi[1] : t == 2 ? phi[2] : phi[3];
+        a1[mt][2] = t == 0 ? plo[4] : 0u;
+        a1[mt][3] = t == 0 ? phi[4] : 0u;
+    }
+    // layer 1 + tanh, re-packed in registers as the layer-2 A fragments A2[mt][kt]
+    uint32_t A2[2][4][4];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_bf16_16816(c, a0, a1, a2, a3, __ldg(P + CP_F1 + (nt * 32 + lane) * 2),
-                           __ldg(P + CP_F1 + (nt * 32 + lane) * 2 + 1));
-            const float bb0 = __ldg(Pf + CP_B1 + 8 * nt + 2 * t), bb1 = __ldg(Pf + CP_B1 + 8 * nt + 2 * t + 1);
-            const uint32_t lo = pack_bf16x2(tanh_mufu(c[0] + bb0), tanh_mufu(c[1] + bb1));  // row g
-            const uint32_t hi = pack_bf16x2(tanh_mufu(c[2] + bb0), tanh_mufu(c[3] + bb1));  // row g+8
-            const int kt = nt >> 1;
-            if ((nt & 1) == 0) {
-                A2[kt][0] = lo;
-                A2[kt][1] = hi;
-            } else {
-                A2[kt][2] = lo;
-                A2[kt][3] = hi;
+    for (int nt = 0; nt < 8; ++nt) {
+        const uint2 b = ldg_pair(P + CP_F1 + (nt * 32 + lane) * 2);
+        const float2 bb = ldg_pair(Pf + CP_B1 + 8 * nt + 2 * t);
+        const int kt = nt >> 1, h = (nt & 1) * 2;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            float c[4];
+            mma_bf16_16816(c, a1[mt], b, bb.x, bb.y, bb.x, bb.y);
+            A2[mt][kt][h] = pack_bf16x2(tanh_mufu(c[0]), tanh_mufu(c[1]));      // row g
+            A2[mt][kt][h + 1] = pack_bf16x2(tanh_mufu(c[2]), tanh_mufu(c[3]));  // row g+8
+        }
+    }
+    // layer 2 + tanh + output-layer partial sums over this lane's columns 2t, 2t+1 of each n-tile
+    float ylo[2] = {0.f, 0.f}, yhi[2] = {0.f, 0.f};
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int n0 = 8 * nt + 2 * t;
+        const float2 bb = ldg_pair(Pf + CP_B2 + n0);
+        float c[2][4];
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const uint2 b = ldg_pair(P + CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                if (kt == 0)
+                    mma_bf16_16816(c[mt], A2[mt][0], b, bb.x, bb.y, bb.x, bb.y);
+                else
+                    mma_bf16_16816(c[mt], A2[mt][kt], b, c[mt][0], c[mt][1], c[mt][2], c[mt][3]);
             }
         }
-        // layer 2 + tanh + output layer partial sums over this lane's columns
-        float ylo = 0.f, yhi = 0.f;
+        const float2 w = ldg_pair(Pf + CP_W3 + n0);
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt)
-                mma_bf16_16816(c, A2[kt][0], A2[kt][1], A2[kt][2], A2[kt][3],
-                               __ldg(P + CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2),
-                               __ldg(P + CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2 + 1));
-            const int n0 = 8 * nt + 2 * t;
-            const float bb0 = __ldg(Pf + CP_B2 + n0), bb1 = __ldg(Pf + CP_B2 + n0 + 1);
-            const float w0 = __ldg(Pf + CP_W3 + n0), w1 = __ldg(Pf + CP_W3 + n0 + 1);
-            ylo = fmaf(w0, tanh_mufu(c[0] + bb0), fmaf(w1, tanh_mufu(c[1] + bb1), ylo));
-            yhi = fmaf(w0, tanh_mufu(c[2] + bb0), fmaf(w1, tanh_mufu(c[3] + bb1), yhi));
+        for (int mt = 0; mt < 2; ++mt) {
+            ylo[mt] = fmaf(w.x, tanh_mufu(c[mt][0]), fmaf(w.y, tanh_mufu(c[mt][1]), ylo[mt]));
+            yhi[mt] = fmaf(w.x, tanh_mufu(c[mt][2]), fmaf(w.y, tanh_mufu(c[mt][3]), yhi[mt]));
         }
-        // sum over the quad (the 4 lanes sharing rows g, g+8), then hand row r to lane 16 mt + r
-        ylo += __shfl_xor_sync(0xffffffffu, ylo, 1);
-        ylo += __shfl_xor_sync(0xffffffffu, ylo, 2);
-        yhi += __shfl_xor_sync(0xffffffffu, yhi, 1);
-        yhi += __shfl_xor_sync(0xffffffffu, yhi, 2);
+    }
+    // sum over the quad (the 4 lanes sharing rows g, g+8), then hand row r of tile mt to lane 16 mt + r
+    float mine = 0.f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        float lo = ylo[mt], hi = yhi[mt];
+        lo += __shfl_xor_sync(0xffffffffu, lo, 1);
+        lo += __shfl_xor_sync(0xffffffffu, lo, 2);
+        hi += __shfl_xor_sync(0xffffffffu, hi, 1);
+        hi += __shfl_xor_sync(0xffffffffu, hi, 2);
         const unsigned r = lane & 15u;
-        const float vlo = __shfl_sync(0xffffffffu, ylo, 4u * (r & 7u));
-        const float vhi = __shfl_sync(0xffffffffu, yhi, 4u * (r & 7u));
+        const float vlo = __shfl_sync(0xffffffffu, lo, 4u * (r & 7u));
+        const float vhi = __shfl_sync(0xffffffffu, hi, 4u * (r & 7u));
         if ((lane >> 4) == (unsigned)mt) mine = r < 8 ? vlo : vhi;
     }
     return (R)(mine + __ldg(Pf + CP_B3));

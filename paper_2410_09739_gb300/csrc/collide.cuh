@@ -64,9 +64,11 @@ __device__ __forceinline__ void inv3(R& k0, R& k1, R& k2, R u, R u2, R tu, R K)
     const R U = K0 ? k0 : K + k0;
     const R M1 = fmaR(u, U, k1);
     const R M2 = fmaR(u2, U, fmaR(tu, k1, k2));
-    const R h = R(0.5) * M1;
-    const R lo = fmaR(R(0.5), M2, -h);
-    const R hi = fmaR(R(0.5), M2, h);
+    // (M2 -/+ M1) / 2 with both halvings exact: the same roundings as 0.5 M2 -/+ 0.5 M1, and no
+    // separate negation (which costs an instruction in packed f2 arithmetic)
+    const R h2 = R(0.5) * M2;
+    const R lo = fmaR(R(-0.5), M1, h2);
+    const R hi = fmaR(R(0.5), M1, h2);
     const R mid = k0 - M2;
     k0 = lo;
     k1 = mid;
@@ -102,9 +104,9 @@ __device__ __forceinline__ void inv3z(R& k0, R& k1, R& k2, R u, R u2, R tu, R K)
         if constexpr (UZ) M2 = t;
         else M2 = fmaR(u2, U, t);
     }
-    const R h = R(0.5) * M1;
-    const R lo = fmaR(R(0.5), M2, -h);
-    const R hi = fmaR(R(0.5), M2, h);
+    const R h2 = R(0.5) * M2;
+    const R lo = fmaR(R(-0.5), M1, h2);
+    const R hi = fmaR(R(0.5), M1, h2);
     R mid;
     if constexpr (Z0) mid = -M2;
     else mid = k0 - M2;
