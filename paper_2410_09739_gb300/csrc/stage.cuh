@@ -49,6 +49,7 @@ namespace fpc {
 
 inline StepArgs<f2> pair_args(const StepArgs<float>& a);  // step_kernel.cuh
 constexpr int kStageFlagTimeout = 2;
+constexpr unsigned kStageOut = 2;  // output stages (a power of two: stage and phase by shifts)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -273,8 +274,7 @@ __host__ __device__ constexpr int stage_min_blocks(int NCW, bool FORCE, int MODE
 // NCW consumer warps (two cells per thread: tiles of up to 64 NCW cells) and one producer warp.
 template <typename S, bool ODD, int BC, bool FORCE, int MODE, int NCW>
 __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, MODE)) k_step_stage(const StepArgs<f2> a, const FastDiv div_tpp,
-                                                               const unsigned ntiles, const int R, const int nsi,
-                                                               const int nso)
+                                                               const unsigned ntiles, const int R, const int nsi)
 {
     static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y, "periodic box or y walls");
     constexpr bool WALLS = BC == BC_WALLS_Y;
@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, M
     constexpr int TC = 2 * (int)NC;              // entries per slot chunk (cells per tile at most)
     constexpr unsigned CB = TC * sizeof(S);      // bytes per slot chunk
     constexpr unsigned STB = 27u * CB;           // bytes per stage
+    constexpr unsigned nso = kStageOut;          // output stages
     extern __shared__ __align__(128) unsigned char stage_smem[];
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const unsigned rowb = (unsigned)nx * sizeof(S);
@@ -362,17 +363,19 @@ __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, M
             issued |= 1u << k;
         }
         bool ok = true;
-        int ki = 0, ko = 0;
+        int ki = 0;
+        unsigned pin = 0;  // (i / nsi) & 1, kept without dividing
         for (unsigned i = 0; i < nt; ++i) {
+            const unsigned ko = i % nso, pout = (i / nso) & 1u;
             // refill input stage ki with tile i + nsi once the consumers have read tile i from it
             if (i + nsi < nt) {
-                ok = mbar_wait_or_abort(empty_in + 8u * ki, (i / nsi) & 1u, abort);
+                ok = mbar_wait_or_abort(empty_in + 8u * ki, pin, abort);
                 if (!ok) break;
                 issue_load(i + nsi, ki);
                 lastpar ^= 1u << ki;
             }
             // store tile i once the consumers have written it
-            ok = mbar_wait_or_abort(full_out + 8u * ko, (i / nso) & 1u, abort);
+            ok = mbar_wait_or_abort(full_out + 8u * ko, pout, abort);
             if (!ok) break;
             issue_store(i, ko);
             // the previous tile's output stage is free once its store has read it
@@ -381,8 +384,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, M
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty_out + 8u * (ko == 0 ? nso - 1 : ko - 1));
             }
-            ki = ki + 1 == nsi ? 0 : ki + 1;
-            ko = ko + 1 == nso ? 0 : ko + 1;
+            if (++ki == nsi) {
+                ki = 0;
+                pin ^= 1u;
+            }
         }
         if (!ok && lane == 0) {
             atomicOr(a.flag, kStageFlagTimeout);
@@ -403,9 +408,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, M
     const unsigned im1 = rb + (x == 0 ? (unsigned)nx - 1 : x - 1);  // x - 1 of the first cell
     const unsigned ip2 = rb + (x + 2 == (unsigned)nx ? 0u : x + 2); // x + 1 of the second cell
     const Rates<f2>& rt = a.rates;
-    int ki = 0, ko = 0;
+    int ki = 0;
+    unsigned pin = 0;  // (i / nsi) & 1, kept without dividing
     for (unsigned i = 0; i < nt; ++i) {
-        if (!mbar_wait_or_abort(full_in + 8u * ki, (i / nsi) & 1u, abort)) return;
+        const unsigned ko = i % nso, pout = (i / nso) & 1u;
+        if (!mbar_wait_or_abort(full_in + 8u * ki, pin, abort)) return;
         bool top = false, bot = false;  // this thread's row touches the wall y = ny - 1/2 / y = -1/2
         if (WALLS) {
             const unsigned t = blockIdx.x + i * gridDim.x;
@@ -443,7 +450,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, M
             fine = collide_cell<f2, FORCE, MODE>(g, rt, a.Fx, a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6], rt.om[8],
                                                  rt.om[9], nullptr);
         if (!fine) atomicOr(a.flag, 1);
-        if (i >= (unsigned)nso && !mbar_wait_or_abort(empty_out + 8u * ko, ((i / nso) - 1u) & 1u, abort)) return;
+        if (i >= (unsigned)nso && !mbar_wait_or_abort(empty_out + 8u * ko, pout ^ 1u, abort)) return;
         const uint32_t aout = out0 + (unsigned)ko * STB;
         const uint32_t qa = aout + ES * ia, qm1 = aout + ES * im1, qp2 = aout + ES * ip2;
         if (act) {
@@ -474,8 +481,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, M
         }
         fence_proxy_async_smem();
         mbar_arrive(full_out + 8u * ko);
-        ki = ki + 1 == nsi ? 0 : ki + 1;
-        ko = ko + 1 == nso ? 0 : ko + 1;
+        if (++ki == nsi) {
+            ki = 0;
+            pin ^= 1u;
+        }
     }
 }
 
@@ -487,12 +496,12 @@ inline int stage_rows(int nx, int ny, int cap)
     return 1;
 }
 
-// Launch: one CTA per resident slot (persistent); nsi input and nso = 2 output stages.
+// Launch: one CTA per resident slot (persistent); nsi input and kStageOut output stages.
 template <typename S, bool ODD, int BC, bool FORCE, int MODE, int NCW>
 cudaError_t step_go_stage_ncw(const StepArgs<float>& a, int nsi, cudaStream_t st)
 {
     constexpr int TC = 64 * NCW;
-    constexpr int nso = 2;
+    constexpr int nso = kStageOut;
     const int R = stage_rows(a.nx, a.ny, TC);
     const int threads = 32 * (NCW + 1);
     const size_t smem = (size_t)(nsi + nso) * 27 * TC * sizeof(S) + 16 * (size_t)(nsi + nso) + 16;
@@ -526,7 +535,7 @@ cudaError_t step_go_stage_ncw(const StepArgs<float>& a, int nsi, cudaStream_t st
     const unsigned ntiles = (unsigned)(a.ny / R) * (unsigned)a.nz;
     unsigned grid = (unsigned)(per_sm * sms);
     if (grid > ntiles) grid = ntiles;
-    kern<<<grid, threads, smem, st>>>(pair_args(a), make_fastdiv((unsigned)(a.ny / R)), ntiles, R, nsi, nso);
+    kern<<<grid, threads, smem, st>>>(pair_args(a), make_fastdiv((unsigned)(a.ny / R)), ntiles, R, nsi);
     return cudaGetLastError();
 }
 
