@@ -301,11 +301,6 @@ def kernel_name(F, workload, launch):
         return ("fpc::k_step_stage (AA even/odd; whole slot rows through %d shared-memory stages by bulk "
                 "asynchronous copies, two cells per thread, blocks of %d; collision mode %d: %s)"
                 % (launch["minb"], launch["block"], launch["mode"], F.LAUNCH_MODES.get(launch["mode"], "?")))
-    if v == 4:
-        return ("fpc::k_step_stage_ip (AA even/odd; whole slot rows through %d shared-memory stages by bulk "
-                "asynchronous copies issued between tiles, output written in place, two cells per thread, "
-                "blocks of %d; collision mode %d: %s)"
-                % (launch["minb"], launch["block"], launch["mode"], F.LAUNCH_MODES.get(launch["mode"], "?")))
     if v == 2:
         base = "fpc::k_ens_pair" if ens else "fpc::k_step_pair"
         shape = "two cells per thread, blocks of 128"

@@ -273,13 +273,11 @@ FPCLBM_API int fpclbm_test_alloc_hook(int fail_after, long long* live);
  * the first fpclbm_step since the last change of parameters, force or wall
  * velocity (the autotuner chooses then); before that FPCLBM_ERR_STATE.
  * out[0] threads per block; out[1] register-cap class (resident blocks of the
- * one-cell kernel: 1 none, 2 ~128, 3 ~80, 4 64 registers), or for variants 3
- * and 4 their number of shared-memory stages; out[2] variant (0 one cell per
- * thread, 1 cp.async-pipelined, 2 two cells per thread on the packed fp32 pipe,
- * 3 two cells per thread with whole slot rows moved through shared memory by
- * bulk asynchronous copies issued by a producer warp, 4 the same with the
- * copies issued between tiles by the computing warps and each tile's output
- * written in place (16-bit storage); ensembles: 0 or 2); out[3] collision mode (0 FP, 1 MCM,
+ * one-cell kernel: 1 none, 2 ~128, 3 ~80, 4 64 registers), or for variant 3
+ * its number of shared-memory stages; out[2] variant (0 one cell per thread,
+ * 1 cp.async-pipelined, 2 two cells per thread on the packed fp32 pipe, 3 two
+ * cells per thread with whole slot rows moved through shared memory by bulk
+ * asynchronous copies; ensembles: 0 or 2); out[3] collision mode (0 FP, 1 MCM,
  * 2 FP + learned closure, 3 FP + Smagorinsky, 4 FP, 5 MCM and 6 FP + learned
  * closure with every rate of orders 3-6 equal to 1, where those moments are set
  * to their attractors plus half their body-force sources).  out is

@@ -291,7 +291,7 @@ cudaError_t one_step(fpclbm* h, long long t, cudaStream_t st, int block, int min
         return launch_ens_step((int)(t & 1), has_force(h), mode_of(h), make_ens_args(h), block, minb, grid, pipe, st);
     const StepArgs<double> a64 = make_args<double>(h);
     const StepArgs<float> a32 = make_args<float>(h);
-    StepLaunch cfg{block, minb, pipe, pipe >= 3 ? grid : 2};  // variants 3 and 4 keep their stage count in grid
+    StepLaunch cfg{block, minb, pipe, pipe == 3 ? grid : 2};  // variant 3 keeps its stage count in grid
     return launch_step(h->precision, (int)(t & 1), kernel_bc(h), has_force(h), mode_of(h), a64, a32, cfg, st);
 }
 
@@ -391,18 +391,16 @@ void save_tune_file()
 
 // FPCLBM_LAUNCH = "block:minb:variant[:stages]" forces a single-box launch configuration
 // (variant 0: one cell per thread, 1: cp.async-pipelined, 2: two cells per thread, 3: two cells
-// per thread through row-staged shared memory with `stages` input stages, 2..6, default 2; 4: the
-// same without a producer warp, written in place, 16-bit storage, default 3 stages).
+// per thread through row-staged shared memory with `stages` input stages, 2..6, default 2).
 bool forced_launch(TuneChoice& c)
 {
     const char* v = std::getenv("FPCLBM_LAUNCH");
     if (!v || !v[0]) return false;
-    int b = 0, m = 0, p = 0, ns = 0;
+    int b = 0, m = 0, p = 0, ns = 2;
     const int got = std::sscanf(v, "%d:%d:%d:%d", &b, &m, &p, &ns);
-    if (got < 4) ns = p == 4 ? 3 : 2;
-    if (got < 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4 || p < 0 || p > 4 || ns < 2 || ns > 6)
+    if (got < 3 || b < 32 || b > 256 || b % 32 || m < 1 || m > 4 || p < 0 || p > 3 || ns < 2 || ns > 6)
         return false;
-    c = {b, m, p >= 3 ? ns : 0, p};
+    c = {b, m, p == 3 ? ns : 0, p};
     return true;
 }
 
@@ -421,13 +419,6 @@ bool stage_ok(const fpclbm* h)
 
 // Threads of a row-staged block: 4 or 8 consumer warps and one producer warp.
 int stage_threads(const fpclbm* h) { return h->boxes[0].nx <= 256 ? 160 : 288; }
-
-// Whether the in-place staged variant (no producer warp) can run this handle: what the row-staged
-// variant needs, 16-bit storage and rows of at most 256 cells.
-bool stage_ip_ok(const fpclbm* h)
-{
-    return stage_ok(h) && elem_size(h->precision) == 2 && h->boxes[0].nx <= 256;
-}
 
 std::string tune_key(const fpclbm* h)
 {
@@ -471,8 +462,6 @@ int autotune(fpclbm* h)
         if (pair_ok) cands.push_back({128, 2, 0, 2});  // 4 blocks of 128 threads, 128 registers
         if (stage_ok(h))  // row-staged paired variant with 2 or 3 input stages
             for (int ns : {2, 3}) cands.push_back({stage_threads(h), 2, ns, 3});
-        if (stage_ip_ok(h))  // in place, without a producer warp, 3 or 4 stages
-            for (int ns : {3, 4}) cands.push_back({128, 2, ns, 4});
     } else if (learned_mode(mode_of(h)) && h->precision != FPCLBM_FP64 && fixed_walls) {
         // two cells per thread first (the collision on the packed fp32 pipe, the MLP once per
         // lane), then one cell per thread capped at 128 registers or uncapped
@@ -502,15 +491,13 @@ int autotune(fpclbm* h)
         return FPCLBM_OK;
     }
     if (!h->ensemble && forced_launch(forced)) {
-        if (forced.pipe == 4 && !stage_ip_ok(h)) forced.pipe = 3;
         if (forced.pipe == 3 && !stage_ok(h)) forced.pipe = pair_ok ? 2 : 0;
         const bool pair_learned = learned_mode(mode_of(h)) && h->precision != FPCLBM_FP64 &&
                                   (kb == BC_PERIODIC || kb == BC_WALLS_Y);
         if ((forced.pipe == 1 && !pipe_ok) || (forced.pipe == 2 && !pair_ok && !pair_learned)) forced.pipe = 0;
-        if (forced.pipe >= 2) forced.minb = 2;
+        if (forced.pipe == 2 || forced.pipe == 3) forced.minb = 2;
         if (forced.pipe == 3) forced.block = stage_threads(h);
-        if (forced.pipe == 4) forced.block = 128;
-        if (forced.pipe < 3) forced.grid = 0;
+        if (forced.pipe != 3) forced.grid = 0;
         if (!fp32_math && !learned_mode(mode_of(h))) forced.minb = 1;  // learned: 1 or 2 (else 1)
         h->block = forced.block;
         h->minb = forced.minb;
@@ -885,7 +872,7 @@ int fpclbm_get_launch(fpclbm_t h, int out[4])
     h->err.clear();
     if (!h->tuned) return fail(h, FPCLBM_ERR_STATE, "no launch chosen yet: the autotuner runs at the first step");
     out[0] = h->block;
-    out[1] = h->pipe >= 3 ? h->grid : h->minb;  // variants 3 and 4: their shared-memory stages
+    out[1] = h->pipe == 3 ? h->grid : h->minb;  // variant 3: its shared-memory stages
     out[2] = h->pipe;
     out[3] = mode_of(h);
     return FPCLBM_OK;

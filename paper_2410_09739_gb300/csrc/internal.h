@@ -14,9 +14,8 @@ struct StepLaunch {
     int minb = 2;  // register-cap variant: minimum resident blocks of 256 threads per SM (2, 3 or 4)
     int pipe = 0;  // 1: software-pipelined persistent variant (cp.async prefetch), 4/8-byte storage only;
                    // 2: paired variant (two cells per thread on the packed fp32 pipe);
-                   // 3: row-staged paired variant (bulk copies of whole slot rows through shared memory);
-                   // 4: the same without a producer warp, output written in place (16-bit storage)
-    int stages = 2;  // variants 3 and 4: shared-memory input stages per block (2..6)
+                   // 3: row-staged paired variant (bulk copies of whole slot rows through shared memory)
+    int stages = 2;  // variant 3: shared-memory input stages per block (2..6)
 };
 
 // One time step of a single box.  odd selects the AA-pattern parity (0: own

@@ -562,233 +562,4 @@ cudaError_t step_go_stage(const StepArgs<float>& a, int nsi, cudaStream_t st)
     return step_go_stage_ncw<S, ODD, BC, FORCE, MODE, 8>(a, nsi, st);
 }
 
-
-// ---------------------------------------------------------------------------------------------
-// Launch variant 4: the same tiles, cells and arithmetic as variant 3 without a producer warp.
-// Each tile's output is written in place into its input stage, so a block of 4 warps (tiles of up
-// to 256 cells) holds `ns` stages and nothing else (ns x 27 slot chunks: 41.5 KB for 16-bit
-// storage at ns = 3), and five blocks fit an SM at 96 registers (the unit-rate collision without
-// force): 20 computing warps against the 16 of variant 3.  Lanes 0..26 of warp 0 issue the bulk copies between their own tiles.  Handshakes
-// per stage k, one phase per use:
-//   full[k]  the tile's rows have landed (expected bytes; one arrival by lane 0 of warp 0)
-//   rd[k]    every thread has read its inputs (odd step only: a thread writes the entries x - 1
-//            and x + 2 that its neighbours read)
-//   wr[k]    every thread has written its outputs; warp 0 then stores the tile from the stage, and
-//            once that store has read it (checked one tile later) loads tile i + ns into it.
-// Warp 0 takes every wait's outcome by a warp vote, so its lanes leave the loop together.  Every
-// wait is bounded as in variant 3 (shared abort word, flag bit 2, copies in flight drained).
-// Resident blocks the registers are capped for: five (96 registers) for the unit-rate collision
-// without force, which fits them without spilling; four (128) for the other modes.
-__host__ __device__ constexpr int stage_ip_min_blocks(bool FORCE, int MODE) { return r1_mode(MODE) && !FORCE ? 5 : 4; }
-
-template <typename S, bool ODD, int BC, bool FORCE, int MODE>
-__global__ void __launch_bounds__(128, stage_ip_min_blocks(FORCE, MODE)) k_step_stage_ip(const StepArgs<f2> a, const FastDiv div_tpp,
-                                                          const unsigned ntiles, const int R, const int ns)
-{
-    static_assert(BC == BC_PERIODIC || BC == BC_WALLS_Y, "periodic box or y walls");
-    constexpr bool WALLS = BC == BC_WALLS_Y;
-    constexpr unsigned NC = 128;            // threads
-    constexpr int TC = 2 * (int)NC;         // entries per slot chunk (cells per tile at most)
-    constexpr unsigned ES = sizeof(S);
-    constexpr unsigned CB = TC * ES;        // bytes per slot chunk
-    constexpr unsigned STB = 27u * CB;      // bytes per stage
-    extern __shared__ __align__(128) unsigned char stage_smem[];
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const unsigned rowb = (unsigned)nx * ES;
-    const unsigned tpp = (unsigned)(ny / R);  // tiles per plane
-    const uint32_t sm0 = smem_addr(stage_smem);
-    const uint32_t bars = sm0 + (unsigned)ns * STB;
-    const uint32_t full = bars, rd = bars + 8u * ns, wr = bars + 16u * ns;
-    volatile int* abort = reinterpret_cast<volatile int*>(stage_smem + (size_t)ns * STB + 24u * ns);
-    const unsigned tid = threadIdx.x, lane = tid & 31u;
-    const bool issuer = tid < 32u;  // warp 0
-    const bool mover = tid < 27u;   // lane s moves slot s
-    unsigned char* const gbuf = static_cast<unsigned char*>(a.buf);
-    const size_t slotb = (size_t)a.stride * ES;
-
-    if (tid == 0) {
-        for (int k = 0; k < ns; ++k) {
-            mbar_init(full + 8u * k, 1);
-            mbar_init(rd + 8u * k, NC);
-            mbar_init(wr + 8u * k, NC);
-        }
-        *abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        fence_proxy_async_smem();
-    }
-    __syncthreads();
-
-    // this CTA's tiles: t_i = blockIdx.x + i gridDim.x, i < nt
-    const unsigned nt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    auto tile_yz = [&](unsigned i, int& y0, int& z) {
-        const unsigned t = blockIdx.x + i * gridDim.x;
-        z = (int)fdiv(t, div_tpp);
-        y0 = (int)(t - (unsigned)z * tpp) * R;
-    };
-    auto gaddr = [&](const RowSpan& q) {
-        return gbuf + (size_t)q.slot * slotb + (size_t)((unsigned)q.y + (unsigned)ny * (unsigned)q.z) * rowb;
-    };
-    // called by all lanes of warp 0
-    auto issue_load = [&](unsigned i, int k) {
-        int y0, z;
-        tile_yz(i, y0, z);
-        const uint32_t bar = full + 8u * k;
-        if (lane == 0) mbar_arrive_expect_tx(bar, 27u * (unsigned)R * rowb);
-        __syncwarp();
-        if (mover) {
-            RowSpan sp[2];
-            const int n = stage_spans<ODD, BC>(false, (int)lane, y0, z, R, ny, nz, sp);
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (q < n)
-                    bulk_load(sm0 + (unsigned)k * STB + lane * CB + (unsigned)sp[q].lr * rowb, gaddr(sp[q]),
-                              (unsigned)sp[q].rows * rowb, bar);
-        }
-    };
-    auto issue_store = [&](unsigned i, int k) {
-        int y0, z;
-        tile_yz(i, y0, z);
-        if (mover) {
-            RowSpan sp[2];
-            const int n = stage_spans<ODD, BC>(true, (int)lane, y0, z, R, ny, nz, sp);
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (q < n)
-                    bulk_store(gaddr(sp[q]), sm0 + (unsigned)k * STB + lane * CB + (unsigned)sp[q].lr * rowb,
-                               (unsigned)sp[q].rows * rowb);
-            bulk_commit();
-        }
-    };
-
-    unsigned lastpar = 0;  // bit k: parity of the phase of the last load issued into stage k
-    unsigned issued = 0;   // bit k: stage k has received a load
-    if (issuer) {
-        const unsigned pro = nt < (unsigned)ns ? nt : (unsigned)ns;
-        for (unsigned k = 0; k < pro; ++k) {
-            issue_load(k, (int)k);
-            issued |= 1u << k;
-        }
-    }
-
-    // cells x, x + 1 of local row r
-    const unsigned half = (unsigned)nx / 2;
-    const unsigned r = tid / half, x = 2u * (tid - r * half);
-    const bool act = r < (unsigned)R;
-    const unsigned rb = r * (unsigned)nx;
-    const unsigned ia = rb + x;                                     // the cells' own entries
-    const unsigned im1 = rb + (x == 0 ? (unsigned)nx - 1 : x - 1);  // x - 1 of the first cell
-    const unsigned ip2 = rb + (x + 2 == (unsigned)nx ? 0u : x + 2); // x + 1 of the second cell
-    const Rates<f2>& rt = a.rates;
-    int k = 0;
-    unsigned ph = 0;  // (i / ns) & 1
-    bool ok = true;
-    for (unsigned i = 0; i < nt; ++i) {
-        bool w = mbar_wait_or_abort(full + 8u * k, ph, abort);
-        if (issuer) w = __all_sync(0xffffffffu, w);
-        if (!w) {
-            ok = false;
-            break;
-        }
-        bool top = false, bot = false;  // this thread's row touches the wall y = ny - 1/2 / y = -1/2
-        if (WALLS) {
-            const unsigned t = blockIdx.x + i * gridDim.x;
-            const unsigned y = (t - fdiv(t, div_tpp) * tpp) * (unsigned)R + r;
-            bot = y == 0;
-            top = y + 1 == (unsigned)ny;
-        }
-        const uint32_t base = sm0 + (unsigned)k * STB;
-        const uint32_t pa = base + ES * ia, pm1 = base + ES * im1, pp2 = base + ES * ip2;
-        f2 g[27];
-        if (act) stage_read<S, ODD, WALLS, CB>(g, pa, pm1, pp2, bot, top);
-        if (ODD) mbar_arrive(rd + 8u * k);
-        bool fine = true;
-        if (act)
-            fine = collide_cell<f2, FORCE, MODE>(g, rt, a.Fx, a.Fy, a.Fz, rt.om[4], rt.om[5], rt.om[6], rt.om[8],
-                                                 rt.om[9], nullptr);
-        if (!fine) atomicOr(a.flag, 1);
-        if (ODD) {
-            w = mbar_wait_or_abort(rd + 8u * k, ph, abort);
-            if (issuer) w = __all_sync(0xffffffffu, w);
-            if (!w) {
-                ok = false;
-                break;
-            }
-        }
-        if (act) stage_write<S, ODD, WALLS, CB>(g, pa, pm1, pp2, bot, top);
-        fence_proxy_async_smem();
-        mbar_arrive(wr + 8u * k);
-        if (issuer) {
-            w = __all_sync(0xffffffffu, mbar_wait_or_abort(wr + 8u * k, ph, abort));
-            if (!w) {
-                ok = false;
-                break;
-            }
-            issue_store(i, k);
-            // the previous tile's stage is free once its store has read it: refill it
-            if (i >= 1 && i - 1 + (unsigned)ns < nt) {
-                const int kp = k == 0 ? ns - 1 : k - 1;
-                if (mover) bulk_wait_read_all_but_last();
-                issue_load(i - 1 + (unsigned)ns, kp);
-                lastpar ^= 1u << kp;
-            }
-        }
-        if (++k == ns) {
-            k = 0;
-            ph ^= 1u;
-        }
-    }
-    if (issuer) {
-        if (!ok && lane == 0) {
-            atomicOr(a.flag, kStageFlagTimeout);
-            // let the loads still in flight land before the CTA's shared memory is released
-            for (int q = 0; q < ns; ++q)
-                if (issued & (1u << q)) mbar_wait_bounded(full + 8u * q, (lastpar >> q) & 1u);
-        }
-        if (mover) bulk_wait_all();
-    }
-}
-
-// Launch of variant 4: one CTA per resident slot (persistent), ns stages, rows of at most 256
-// cells, 16-bit storage.
-template <typename S, bool ODD, int BC, bool FORCE, int MODE>
-cudaError_t step_go_stage_ip(const StepArgs<float>& a, int ns, cudaStream_t st)
-{
-    if (sizeof(S) != 2 || (a.nx * sizeof(S)) % 16 != 0 || a.nx > 256 || a.nx < 2 || ns < 2 || ns > 6)
-        return cudaErrorInvalidValue;
-    constexpr int TC = 256;
-    const int R = stage_rows(a.nx, a.ny, TC);
-    const int threads = 128;
-    const size_t smem = (size_t)ns * 27 * TC * sizeof(S) + 24 * (size_t)ns + 16;
-    auto kern = k_step_stage_ip<S, ODD, BC, FORCE, MODE>;
-    static int c_dev = -1, c_per_sm = 0, c_sms = 0;  // as in step_go_stage_ncw
-    static size_t c_smem = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0;
-    if (dev == c_dev && smem == c_smem) {
-        per_sm = c_per_sm;
-        sms = c_sms;
-    } else {
-        int optin = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e != cudaSuccess) return e;
-        if (smem > (size_t)optin) return cudaErrorInvalidValue;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        c_per_sm = per_sm;
-        c_sms = sms;
-        c_smem = smem;
-        c_dev = dev;
-    }
-    const unsigned ntiles = (unsigned)(a.ny / R) * (unsigned)a.nz;
-    unsigned grid = (unsigned)(per_sm * sms);
-    if (grid > ntiles) grid = ntiles;
-    kern<<<grid, threads, smem, st>>>(pair_args(a), make_fastdiv((unsigned)(a.ny / R)), ntiles, R, ns);
-    return cudaGetLastError();
-}
-
 }  // namespace fpc

@@ -243,10 +243,6 @@ cudaError_t step_go(const StepArgs<R>& a, const StepLaunch& cfg, cudaStream_t st
         // row-staged variant (stage.cuh): periodic boxes and channels
         if constexpr (BC == BC_PERIODIC || BC == BC_WALLS_Y) {
             if (cfg.pipe == 3) return step_go_stage<S, ODD, BC, FORCE, MODE>(a, cfg.stages, st);
-            // in-place staged variant without a producer warp: 16-bit storage only
-            if constexpr (sizeof(S) == 2) {
-                if (cfg.pipe == 4) return step_go_stage_ip<S, ODD, BC, FORCE, MODE>(a, cfg.stages, st);
-            }
         }
     }
     // the pipelined variant retires tail lanes early, so it never runs the warp-collective

@@ -10,10 +10,7 @@ the oracle it meets the fp32 path's bound of 1e-6 absolute per step.
 
 Forced with FPCLBM_LAUNCH = "128:2:3[:stages]"; the variant needs rows of a multiple of 16 bytes
 (nx a multiple of 8 for 16-bit storage, of 4 for fp32) and falls back to the paired kernel
-otherwise.  Launch variant 4 ("128:2:4[:stages]") is the same tiling without a producer warp: the
-computing warps issue the bulk copies between tiles and write each tile's output in place into its
-input stage.  It takes 16-bit storage and rows of at most 256 cells (else variant 3 runs), and must
-equal the paired kernel bit for bit as well.
+otherwise.
 """
 import numpy as np
 import pytest
@@ -52,48 +49,33 @@ def run(monkeypatch, launch, shape, prec, bc, force, mode, drift, f0, n):
 MODES = [(0, 0.3), (0, 0.0), (1, 0.3), (1, 0.0)]
 
 
-# (variant, storage): variant 4 takes 16-bit storage only (its fallback is checked separately)
-STAGED = [(3, "bf16"), (3, "fp16"), (3, "fp32"), (4, "bf16"), (4, "fp16")]
-
-
-@pytest.mark.parametrize("variant,prec", STAGED)
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp32"])
 @pytest.mark.parametrize("shape", [(8, 3, 2), (16, 5, 3), (24, 7, 6), (40, 9, 5)])
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("force", [False, True])
 @pytest.mark.parametrize("mode,drift", MODES)
-def test_stage_equals_paired_bitwise(monkeypatch, variant, prec, shape, bc, force, mode, drift):
+def test_stage_equals_paired_bitwise(monkeypatch, prec, shape, bc, force, mode, drift):
     nx, ny, nz = shape
     f0 = near_eq(nx, ny, nz, 7 * nx + ny + 3 * nz + bc + 2 * force + 4 * mode)
     for n in (1, 2, 5):
         _, a, la = run(monkeypatch, "128:2:2", shape, prec, bc, force, mode, drift, f0, n)
-        _, b, lb = run(monkeypatch, "128:2:%d" % variant, shape, prec, bc, force, mode, drift, f0, n)
-        assert la["variant"] == 2 and lb["variant"] == variant
+        _, b, lb = run(monkeypatch, "128:2:3", shape, prec, bc, force, mode, drift, f0, n)
+        assert la["variant"] == 2 and lb["variant"] == 3
         assert np.array_equal(a, b), (n, float(np.max(np.abs(a - b))))
 
 
-@pytest.mark.parametrize("variant,prec", [(3, "bf16"), (3, "fp32"), (4, "bf16")])
-@pytest.mark.parametrize("stages", [2, 3, 4, 6])
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("stages", [3, 4, 6])
 @pytest.mark.parametrize("shape,bc", [((64, 32, 31), 1), ((48, 20, 16), 0)])
-def test_stage_equals_paired_many_steps(monkeypatch, variant, prec, stages, shape, bc):
+def test_stage_equals_paired_many_steps(monkeypatch, prec, stages, shape, bc):
     """40 steps (the captured-graph path, both parities many times) with force in a channel, and
-    ring depths 2, 3, 4 and 6: more rows than CTAs, so every CTA cycles its stages."""
+    ring depths 3, 4 and 6: more rows than CTAs, so every CTA cycles its stages."""
     nx, ny, nz = shape
     f0 = near_eq(nx, ny, nz, 91 + stages)
     _, a, _ = run(monkeypatch, "128:2:2", shape, prec, bc, True, 0, 0.0, f0, 40)
-    _, b, lb = run(monkeypatch, "128:2:%d:%d" % (variant, stages), shape, prec, bc, True, 0, 0.0, f0, 40)
-    assert lb["variant"] == variant
+    _, b, lb = run(monkeypatch, "128:2:3:%d" % stages, shape, prec, bc, True, 0, 0.0, f0, 40)
+    assert lb["variant"] == 3
     assert np.array_equal(a, b), float(np.max(np.abs(a - b)))
-
-
-@pytest.mark.parametrize("prec,shape", [("fp32", (16, 5, 3)), ("bf16", (264, 4, 3)), ("fp16", (320, 3, 2))])
-def test_stage_in_place_falls_back_to_row_staged(monkeypatch, prec, shape):
-    """Variant 4 on fp32 storage or rows longer than 256 cells runs variant 3, with the same result."""
-    nx, ny, nz = shape
-    f0 = near_eq(nx, ny, nz, 17)
-    _, a, la = run(monkeypatch, "128:2:4", shape, prec, 1, True, 0, 0.0, f0, 3)
-    _, b, _ = run(monkeypatch, "128:2:2", shape, prec, 1, True, 0, 0.0, f0, 3)
-    assert la["variant"] == 3
-    assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("shape", [(8, 1, 1), (4, 4, 4), (16, 9, 5), (32, 7, 6)])
@@ -111,20 +93,19 @@ def test_stage_fp32_matches_oracle(monkeypatch, shape, bc, force, mode, drift):
         assert np.max(np.abs(got - ref)) <= 1e-6 * n, n
 
 
-@pytest.mark.parametrize("variant", [3, 4])
 @pytest.mark.parametrize("prec,shape", [("bf16", (12, 4, 4)), ("fp16", (20, 3, 3)), ("fp32", (6, 4, 4))])
-def test_stage_falls_back_when_rows_are_not_16_byte_multiples(monkeypatch, variant, prec, shape):
+def test_stage_falls_back_when_rows_are_not_16_byte_multiples(monkeypatch, prec, shape):
     nx, ny, nz = shape
     f0 = near_eq(nx, ny, nz, 3)
-    _, a, la = run(monkeypatch, "128:2:%d" % variant, shape, prec, 1, True, 0, 0.0, f0, 3)
+    _, a, la = run(monkeypatch, "128:2:3", shape, prec, 1, True, 0, 0.0, f0, 3)
     _, b, _ = run(monkeypatch, "128:2:2", shape, prec, 1, True, 0, 0.0, f0, 3)
     assert la["variant"] == 2
     assert np.array_equal(a, b)
 
 
 def test_stage_full_size_bf16_tgv_256_matches_paired(monkeypatch):
-    """The 256^3 BF16 TGV of the bench, 6 steps, both staged variants against paired on sampled
-    cells (every cell of the rows at the box's faces and edges, plus random cells)."""
+    """The 256^3 BF16 TGV of the bench, 6 steps, staged against paired on sampled cells (every
+    cell of the rows at the box's faces and edges, plus random cells)."""
     n = 256
     tau = 3 * W.tgv_viscosity(n, 0.05, 1600.0) + 0.5
     rho, ux, uy, uz = W.tgv(n, 0.05)
@@ -133,7 +114,7 @@ def test_stage_full_size_bf16_tgv_256_matches_paired(monkeypatch):
     cells = np.concatenate([np.arange(n) + n * (y + n * z) for y, z in rows] +
                            [rng.integers(0, n ** 3, 4096)]).astype(np.int64)
     out = []
-    for launch in ("128:2:2", "128:2:3", "128:2:4"):
+    for launch in ("128:2:2", "128:2:3"):
         monkeypatch.setenv("FPCLBM_LAUNCH", launch)
         with F.Lattice(n, n, n, "bf16", F.FPCLBM_BC_PERIODIC) as lat:
             lat.set_params(tau)
@@ -142,4 +123,3 @@ def test_stage_full_size_bf16_tgv_256_matches_paired(monkeypatch):
             assert lat.launch()["variant"] == int(launch[-1])
             out.append(lat.populations_at(cells))
     assert np.array_equal(out[0], out[1])
-    assert np.array_equal(out[0], out[2])
