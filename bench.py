@@ -338,11 +338,12 @@ def closure_weights(seed):
     return ((a + ((a >> 16) & 1) + 0x7FFF) >> 16).astype(np.uint16)
 
 
-def setup(args, F, prec, stream, drift=0.0, learned=True):
-    """Build the lattice of the chosen workload; returns (lat, flat fields, cells, config dict).
-    drift > 0 selects the rates k * drift of orders k >= 3 (TGV only); learned=False runs the
-    closure workload's coarse channel without the closure."""
-    if args.workload == "tgv":
+def setup(args, F, prec, stream, drift=0.0, learned=True, workload=None):
+    """Build the lattice of a workload (default: the chosen one); returns (lat, flat fields,
+    cells, config dict).  drift > 0 selects the rates k * drift of orders k >= 3 (TGV only);
+    learned=False runs the closure workload's coarse channel without the closure."""
+    workload = workload or args.workload
+    if workload == "tgv":
         n, u0 = args.size, 0.05
         tau = 3 * W.tgv_viscosity(n, u0, 1600.0) + 0.5
         lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_PERIODIC, stream=stream)
@@ -351,7 +352,7 @@ def setup(args, F, prec, stream, drift=0.0, learned=True):
         cfg = {"workload": tgv_workload(n, tau)}
         if drift > 0:
             cfg["drift"] = drift
-    elif args.workload == "channel":
+    elif workload == "channel":
         nx, ny, nz, u_star = 384, 192, 192, 0.005
         H = ny / 2
         tau = 3 * (u_star * H / 180.0) + 0.5
@@ -360,7 +361,7 @@ def setup(args, F, prec, stream, drift=0.0, learned=True):
         lat.set_force(u_star ** 2 / H, 0.0, 0.0)
         flds = W.channel_fields(nx, ny, nz, u_star, seed=7)
         cfg = {"workload": "channel Re_tau=180 384x192x192, y walls, body force, tau=%.6f" % tau}
-    elif args.workload == "cavity":
+    elif workload == "cavity":
         n, U0 = 150, 0.1 / 3 ** 0.5
         tau = 0.5 + 3 * U0 * n / 1000.0
         lat = F.Lattice(n, n, n, prec, F.FPCLBM_BC_BOX, stream=stream)
@@ -369,7 +370,7 @@ def setup(args, F, prec, stream, drift=0.0, learned=True):
         one = np.ones((n, n, n))
         flds = (one, 0 * one, 0 * one, 0 * one)
         cfg = {"workload": "lid-driven cubic cavity 150^3, Re=1000, Ma=0.1, walls on all faces, tau=%.6f" % tau}
-    elif args.workload == "closure":
+    elif workload == "closure":
         # the learned closure's coarse channel: 192 x 96 x 96, Re_tau = 395 (H = 48, u* = 0.005), BF16
         # storage by default; the headline leg runs the learned mode with seeded random bf16 weights
         # (the inference cost does not depend on their values), the secondary leg plain FPC-LBM
@@ -387,7 +388,7 @@ def setup(args, F, prec, stream, drift=0.0, learned=True):
         cfg = {"workload": "learned-closure coarse channel Re_tau=395 192x96x96, y walls, body force, tau=%.6f, "
                            "%s" % (tau, "FP + learned closure (MLP 9-64-64-1, random bf16 weights)" if learned
                                    else "plain FP")}
-    elif args.workload == "shear2d":
+    elif workload == "shear2d":
         n, U = 4096, 0.2 / 3 ** 0.5
         tau = 0.5 + 3 * U * n / 30000.0
         lat = F.Lattice2D(n, n, prec, stream=stream)
@@ -425,18 +426,21 @@ def main():
     two_d = args.workload == "shear2d"
     qb = 18 if two_d else 54  # algorithmic bytes per cell update in units of the storage size
     results = {}
-    # legs: the headline line first, then the secondary entries (same workload; 16-bit deviation
-    # storage and, for the TGV, the general-rate kernel with omega_k = k * drift for k >= 3)
-    legs = [("headline", prec0, args.drift, True)]
+    # legs: the headline line first, then the secondary entries: 16-bit deviation storage of the
+    # same workload and, for the TGV, the general-rate kernel with omega_k = k * drift for k >= 3,
+    # the Re_tau = 180 channel (BF16 storage), the 256-box ensemble and the lid-driven cavity
+    legs = [("headline", prec0, args.drift, True, args.workload)]
     if args.workload == "closure":
-        legs.append(("plain_coarse", prec0, 0.0, False))
+        legs.append(("plain_coarse", prec0, 0.0, False, "closure"))
     elif not args.no_variants and args.workload != "ensemble":
-        legs += [(p, p, args.drift, True) for p in ("fp16", "bf16") if p != prec0]
+        legs += [(p, p, args.drift, True, args.workload) for p in ("fp16", "bf16") if p != prec0]
         if args.workload == "tgv" and args.drift == 0.0:
-            legs.append(("fp32_general_rates", "fp32", 0.3, True))
+            legs.append(("fp32_general_rates", "fp32", 0.3, True, "tgv"))
+            legs += [("channel_bf16", "bf16", 0.0, True, "channel"), ("ensemble_fp32", "fp32", 0.0, True, "ensemble"),
+                     ("cavity_fp32", "fp32", 0.0, True, "cavity")]
     cfg = None
-    for key, prec, drift, learned in legs:
-        lat, flat, ncell, c = setup(args, F, prec, stream, drift, learned)
+    for key, prec, drift, learned, wl in legs:
+        lat, flat, ncell, c = setup(args, F, prec, stream, drift, learned, wl)
         if cfg is None:
             cfg = c
         barrier(world)
@@ -447,7 +451,8 @@ def main():
         ck = clocks.stop() if clocks else None
         el = max_over_ranks(el, world)
         results[key] = {"seconds": el, "clocks": ck, "launch": lat.launch() if not two_d else None,
-                        "prec": prec, "drift": drift}
+                        "prec": prec, "drift": drift, "cells": ncell, "workload": wl,
+                        "description": c["workload"]}
         if key == "headline":
             # e2e: host buffers through the C ABI, copies inside the timed region
             nf = 3 if two_d else 4
@@ -471,6 +476,7 @@ def main():
     if rank != 0:
         return
     prec = prec0
+    ncell = results["headline"]["cells"]
     el = results["headline"]["seconds"]
     value = ncell * args.inner * args.steps * world / el / 1e6
     launches = args.inner * args.steps
@@ -506,12 +512,14 @@ def main():
         for key, r in results.items():
             if key == "headline":
                 continue
-            ach = qb * BYTES[r["prec"]] * ncell / (r["seconds"] / launches) / 1e9
+            ach = qb * BYTES[r["prec"]] * r["cells"] / (r["seconds"] / launches) / 1e9
             out["variants"][key] = {
-                "storage": r["prec"], "drift": r["drift"], "MLUPS": ncell * launches * world / r["seconds"] / 1e6,
+                "storage": r["prec"], "drift": r["drift"], "MLUPS": r["cells"] * launches * world / r["seconds"] / 1e6,
                 "ms_per_step": r["seconds"] / args.steps * 1e3, "achieved_gbs": ach, "frac": ach / peak,
                 "frac_nominal": ach / NOMINAL_HBM_GBS, "clocks": r["clocks"],
-                "kernel": kernel_name(F, args.workload, r["launch"])}
+                "kernel": kernel_name(F, r["workload"], r["launch"])}
+            if r["workload"] != args.workload:
+                out["variants"][key]["workload"] = r["description"]
     if world == 1 and not args.no_cpu_baseline:
         if two_d:
             U = 0.2 / 3 ** 0.5
