@@ -2,15 +2,15 @@
 //
 // MLP 9 -> 64 -> 64 -> 1 with tanh hidden layers, evaluated for the 32 cells of
 // a warp at once on the tensor cores: both hidden layers are
-// mma.sync.m16n8k16 bf16 x bf16 -> fp32 products (rows = cells, the 9 inputs
-// padded to K = 16), the output layer and biases in fp32.  The fp32
+// mma.sync.m16n8k16 bf16 x bf16 -> fp32 products (rows = cells, the 9 inputs and
+// a constant 1 for the bias padded to K = 16), the output layer in fp32.  The fp32
 // accumulator fragments of layer 1 are exactly the A-operand fragments of
 // layer 2 (row g / g+8, columns 2t, 2t+1 per n-tile), so the hidden
 // activations never leave registers.  tanh uses the MUFU approximation
 // (relative error ~2^-11, below the bf16 rounding of the activations).
 //
 // The weights are the bf16 values installed by fpclbm_set_closure, re-packed
-// on the host into per-lane fragment order (ClosurePack below).  The function
+// on the host into per-lane fragment order (the layout below).  The function
 // is warp-collective: every lane of the warp must call it (inactive lanes pass
 // any finite inputs and ignore the result).
 #pragma once
@@ -24,10 +24,15 @@ namespace fpc {
 enum { CL_W1 = 0, CL_B1 = 576, CL_W2 = 640, CL_B2 = 4736, CL_W3 = 4800, CL_B3 = 4864, CL_N = 4865 };
 
 // Device layout of the packed closure (32-bit words):
-//   [0, 512)      layer-1 B fragments: (nt * 32 + lane) * 2 + {0, 1}, nt = 0..7
+//   [0, 512)      layer-1 B fragments: (nt * 32 + lane) * 2 + {0, 1}, nt = 0..7; K column 9
+//                 holds b1 (the A operand's input 9 is the constant 1)
 //   [512, 2560)   layer-2 B fragments: ((nt * 4 + kt) * 32 + lane) * 2 + {0, 1}
 //   [2560, 2624)  b1 (fp32), [2624, 2688) b2, [2688, 2752) W3, [2752] b3
-enum { CP_F1 = 0, CP_F2 = 512, CP_B1 = 2560, CP_B2 = 2624, CP_W3 = 2688, CP_B3 = 2752, CP_WORDS = 2756 };
+//   [2756, 3012)  layer-2 bias fragments: nt * 32 + lane, the first word of the B fragment of a
+//                 K tile whose only non-zero row holds b2 (the second word is zero)
+// The weights, biases included, are bf16 values, so b1 and b2 enter the products exactly.
+enum { CP_F1 = 0, CP_F2 = 512, CP_B1 = 2560, CP_B2 = 2624, CP_W3 = 2688, CP_B3 = 2752, CP_F2B = 2756,
+       CP_WORDS = 3012 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
@@ -71,21 +76,22 @@ __device__ __forceinline__ uint2 ldg_pair(const uint32_t* p) { return __ldg(rein
 __device__ __forceinline__ float2 ldg_pair(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
 
 // delta omega of this lane's cell from its 9 inputs (warp-collective).  The warp's 32 cells form
-// two 16-row tiles; every weight fragment and bias pair is loaded once and used by both tiles, and
-// the biases enter each product as its accumulator input.
+// two 16-row tiles; every weight fragment is loaded once and used by both tiles.  The biases enter
+// the products as weights of a constant input 1: b1 in the spare K column 9 of layer 1, b2 in a
+// fifth K tile of layer 2 whose A fragment is the constant 1 in column 64.
 template <typename R>
 __device__ R closure_delta_omega(const uint32_t* __restrict__ P, const R in[9])
 {
     __syncwarp();  // the .aligned mma below needs the whole warp converged
     const unsigned lane = threadIdx.x & 31u, g = lane >> 2, t = lane & 3u;
     const float* Pf = reinterpret_cast<const float*>(P);
-    // this lane's inputs as bf16 pairs (x0,x1) (x2,x3) (x4,x5) (x6,x7) (x8,0)
+    // this lane's inputs as bf16 pairs (x0,x1) (x2,x3) (x4,x5) (x6,x7) (x8,1)
     uint32_t q[5];
     q[0] = pack_bf16x2((float)in[0], (float)in[1]);
     q[1] = pack_bf16x2((float)in[2], (float)in[3]);
     q[2] = pack_bf16x2((float)in[4], (float)in[5]);
     q[3] = pack_bf16x2((float)in[6], (float)in[7]);
-    q[4] = pack_bf16x2((float)in[8], 0.f);
+    q[4] = pack_bf16x2((float)in[8], 1.f);  // input 9: the constant 1 that carries b1
     // layer-1 A fragments of tile mt: rows g and g+8 (cells 16 mt + g, 16 mt + g + 8), K columns
     // 2t, 2t+1 (and + 8: only input 8 and zeros)
     uint32_t a1[2][4];
@@ -103,38 +109,39 @@ __device__ R closure_delta_omega(const uint32_t* __restrict__ P, const R in[9])
         a1[mt][2] = t == 0 ? plo[4] : 0u;
         a1[mt][3] = t == 0 ? phi[4] : 0u;
     }
-    // layer 1 + tanh, re-packed in registers as the layer-2 A fragments A2[mt][kt]
+    // layer 1 (+ b1 through input 9) + tanh, re-packed in registers as the layer-2 A fragments
+    // A2[mt][kt]
     uint32_t A2[2][4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const uint2 b = ldg_pair(P + CP_F1 + (nt * 32 + lane) * 2);
-        const float2 bb = ldg_pair(Pf + CP_B1 + 8 * nt + 2 * t);
         const int kt = nt >> 1, h = (nt & 1) * 2;
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
             float c[4];
-            mma_bf16_16816(c, a1[mt], b, bb.x, bb.y, bb.x, bb.y);
+            mma_bf16_16816(c, a1[mt], b, 0.f, 0.f, 0.f, 0.f);
             A2[mt][kt][h] = pack_bf16x2(tanh_mufu(c[0]), tanh_mufu(c[1]));      // row g
             A2[mt][kt][h + 1] = pack_bf16x2(tanh_mufu(c[2]), tanh_mufu(c[3]));  // row g+8
         }
     }
-    // layer 2 + tanh + output-layer partial sums over this lane's columns 2t, 2t+1 of each n-tile
+    // layer 2 (b2 first, through the constant-1 K tile) + tanh + output-layer partial sums over
+    // this lane's columns 2t, 2t+1 of each n-tile
+    const uint32_t one = t == 0 ? pack_bf16x2(1.f, 0.f) : 0u;  // A fragment: 1 in K column 64
+    const uint32_t aone[4] = {one, one, 0u, 0u};
     float ylo[2] = {0.f, 0.f}, yhi[2] = {0.f, 0.f};
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int n0 = 8 * nt + 2 * t;
-        const float2 bb = ldg_pair(Pf + CP_B2 + n0);
+        const uint2 bias = make_uint2(__ldg(P + CP_F2B + nt * 32 + lane), 0u);
         float c[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma_bf16_16816(c[mt], aone, bias, 0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) {
             const uint2 b = ldg_pair(P + CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2);
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                if (kt == 0)
-                    mma_bf16_16816(c[mt], A2[mt][0], b, bb.x, bb.y, bb.x, bb.y);
-                else
-                    mma_bf16_16816(c[mt], A2[mt][kt], b, c[mt][0], c[mt][1], c[mt][2], c[mt][3]);
-            }
+            for (int mt = 0; mt < 2; ++mt)
+                mma_bf16_16816(c[mt], A2[mt][kt], b, c[mt][0], c[mt][1], c[mt][2], c[mt][3]);
         }
         const float2 w = ldg_pair(Pf + CP_W3 + n0);
 #pragma unroll

@@ -1068,7 +1068,8 @@ int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
     // consecutive k (lower k in the low half): k = 2t, 2t+1 and k = 2t+8, 2t+9
     std::vector<uint32_t> pk(CP_WORDS, 0u);
     auto wb = [&](int idx) -> uint32_t { return w[idx]; };
-    auto w1 = [&](int n, int k) -> uint32_t { return k < 9 ? wb(CL_W1 + 9 * n + k) : 0u; };
+    // layer 1: K column 9 carries b1 (the kernel's input 9 is the constant 1)
+    auto w1 = [&](int n, int k) -> uint32_t { return k < 9 ? wb(CL_W1 + 9 * n + k) : k == 9 ? wb(CL_B1 + n) : 0u; };
     auto w2 = [&](int n, int k) -> uint32_t { return wb(CL_W2 + 64 * n + k); };
     for (int lane = 0; lane < 32; ++lane) {
         const int g = lane / 4, t = lane % 4;
@@ -1081,6 +1082,8 @@ int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
                 pk[CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2] = w2(n, k) | (w2(n, k + 1) << 16);
                 pk[CP_F2 + ((nt * 4 + kt) * 32 + lane) * 2 + 1] = w2(n, k + 8) | (w2(n, k + 9) << 16);
             }
+            // layer 2's bias as a fifth K tile whose only non-zero row (k = 64, input 1) holds b2
+            pk[CP_F2B + nt * 32 + lane] = t == 0 ? wb(CL_B2 + n) : 0u;
         }
     }
     for (int j = 0; j < 64; ++j) {
