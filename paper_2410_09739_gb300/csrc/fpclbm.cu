@@ -417,8 +417,12 @@ bool stage_ok(const fpclbm* h)
     return (b.nx * es) % 16 == 0 && b.nx <= 512;
 }
 
-// Threads of a row-staged block: 4 or 8 consumer warps and one producer warp.
-int stage_threads(const fpclbm* h) { return h->boxes[0].nx <= 256 ? 160 : 288; }
+// Threads of a row-staged block: 4, 6 or 8 consumer warps and one producer warp.
+int stage_threads(const fpclbm* h)
+{
+    const int nx = h->boxes[0].nx;
+    return nx <= 256 ? 160 : nx <= 384 ? 224 : 288;
+}
 
 std::string tune_key(const fpclbm* h)
 {

@@ -321,10 +321,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 
 // Resident blocks per SM the registers are capped for: four blocks of 4 consumer warps (96
 // registers) for the unit-rate collision without force, which fits them without spilling, three
-// for the other modes, one block of 8 consumer warps.
+// for the other modes; two blocks of 6 consumer warps (146 registers); one block of 8.
 __host__ __device__ constexpr int stage_min_blocks(int NCW, bool FORCE, int MODE)
 {
-    return NCW != 4 ? 1 : (r1_mode(MODE) && !FORCE) ? 4 : 3;
+    return NCW == 4 ? ((r1_mode(MODE) && !FORCE) ? 4 : 3) : NCW == 6 ? 2 : 1;
 }
 
 // NCW consumer warps (two cells per thread: tiles of up to 64 NCW cells) and one producer warp.
@@ -552,13 +552,14 @@ cudaError_t step_go_stage_ncw(const StepArgs<float>& a, int nsi, cudaStream_t st
     return cudaGetLastError();
 }
 
-// Tiles of up to 256 cells (4 consumer warps) for rows of at most 256 cells, else up to 512
-// (8 consumer warps).
+// Tiles of up to 256 cells (4 consumer warps) for rows of at most 256 cells, of 384 (6 consumer
+// warps, two blocks per SM) for rows of at most 384, else of 512 (8 consumer warps).
 template <typename S, bool ODD, int BC, bool FORCE, int MODE>
 cudaError_t step_go_stage(const StepArgs<float>& a, int nsi, cudaStream_t st)
 {
     if ((a.nx * sizeof(S)) % 16 != 0 || a.nx > 512 || a.nx < 2 || nsi < 2 || nsi > 6) return cudaErrorInvalidValue;
     if (a.nx <= 256) return step_go_stage_ncw<S, ODD, BC, FORCE, MODE, 4>(a, nsi, st);
+    if (a.nx <= 384) return step_go_stage_ncw<S, ODD, BC, FORCE, MODE, 6>(a, nsi, st);
     return step_go_stage_ncw<S, ODD, BC, FORCE, MODE, 8>(a, nsi, st);
 }
 

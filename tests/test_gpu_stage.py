@@ -93,6 +93,22 @@ def test_stage_fp32_matches_oracle(monkeypatch, shape, bc, force, mode, drift):
         assert np.max(np.abs(got - ref)) <= 1e-6 * n, n
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp32"])
+@pytest.mark.parametrize("shape", [(264, 3, 2), (384, 4, 3), (392, 2, 3)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_stage_wide_rows_equal_paired_bitwise(monkeypatch, prec, shape, bc):
+    """Rows of 257-384 cells take tiles of 384 (six consumer warps), longer rows tiles of 512 (eight
+    consumer warps); unit rates with force (the channel's collision) and general rates, two steps."""
+    nx, ny, nz = shape
+    f0 = near_eq(nx, ny, nz, nx + 7 * bc)
+    for mode, drift in ((0, 0.0), (0, 0.3)):
+        _, a, la = run(monkeypatch, "128:2:2", shape, prec, bc, True, mode, drift, f0, 2)
+        _, b, lb = run(monkeypatch, "128:2:3", shape, prec, bc, True, mode, drift, f0, 2)
+        assert la["variant"] == 2 and lb["variant"] == 3
+        assert lb["block"] == (224 if nx <= 384 else 288)
+        assert np.array_equal(a, b), float(np.max(np.abs(a - b)))
+
+
 @pytest.mark.parametrize("prec,shape", [("bf16", (12, 4, 4)), ("fp16", (20, 3, 3)), ("fp32", (6, 4, 4))])
 def test_stage_falls_back_when_rows_are_not_16_byte_multiples(monkeypatch, prec, shape):
     nx, ny, nz = shape
