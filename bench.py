@@ -119,9 +119,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision, n):
-    """dram bytes per launch of the step kernel from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+def ncu_entry(precision):
+    """The committed ncu record of the step kernel for this storage type, if it was taken on the
+    current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
@@ -130,10 +130,30 @@ def ncu_traffic(precision, n):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
-    ent = rec.get("entries", {}).get(precision)
-    if not ent:
+    return rec.get("entries", {}).get(precision)
+
+
+def ncu_traffic(precision, n):
+    """dram bytes per launch of the step kernel (n^3 TGV) from the committed ncu record, or None."""
+    ent = ncu_entry(precision)
+    return float(ent["bytes_per_cell"]) * n ** 3 if ent else None
+
+
+# FP32 lane operations per second of the FMA pipes: 152 SMs x 128 lanes x 2.07 GHz (maximum SM clock)
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
+def alu_roofline(precision, mlups):
+    """The ALU roofline of a 16-bit storage entry: fp32 lane operations per cell (ncu instruction
+    classes of the same kernel source; a packed operation counts two) against the FMA pipes' peak."""
+    ent = ncu_entry(precision)
+    if not ent or "fp32_lane_ops_per_cell" not in ent:
         return None
-    return float(ent["bytes_per_cell"]) * n ** 3
+    ops = float(ent["fp32_lane_ops_per_cell"])
+    ach = mlups * 1e6 * ops / 1e12
+    return {"bound": "alu", "lane_ops_per_cell": ops, "achieved": ach, "peak": ALU_PEAK_TOPS,
+            "unit": "T lane-op/s", "frac": ach / ALU_PEAK_TOPS,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz"}
 
 
 class Clocks:
@@ -520,6 +540,10 @@ def main():
                 "kernel": kernel_name(F, r["workload"], r["launch"])}
             if r["workload"] != args.workload:
                 out["variants"][key]["workload"] = r["description"]
+            elif args.workload == "tgv" and args.size == 256 and r["prec"] in ("fp16", "bf16") and r["drift"] == 0:
+                alu = alu_roofline(r["prec"], out["variants"][key]["MLUPS"])
+                if alu:
+                    out["variants"][key]["alu_roofline"] = alu
     if world == 1 and not args.no_cpu_baseline:
         if two_d:
             U = 0.2 / 3 ** 0.5
