@@ -295,9 +295,6 @@ __device__ __forceinline__ void stage_write(const f2 (&g)[27], uint32_t qa, uint
     }
 }
 
-// CB: bytes of one slot chunk of a stage (a compile-time constant, so that every shared-memory
-// access of the compute phase is an immediate offset); a tile holds R whole rows, R nx <= CB /
-// sizeof(S).
 // Bounded wait on an mbarrier phase that also gives up when another thread of the CTA has
 // aborted; a wait that runs out (about a second) aborts the CTA.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort)
@@ -328,6 +325,9 @@ __host__ __device__ constexpr int stage_min_blocks(int NCW, bool FORCE, int MODE
 }
 
 // NCW consumer warps (two cells per thread: tiles of up to 64 NCW cells) and one producer warp.
+// CB, the bytes of one slot chunk of a stage, is a compile-time constant, so that every
+// shared-memory access of the compute phase is an immediate offset; a tile holds R whole rows,
+// R nx <= CB / sizeof(S).
 template <typename S, bool ODD, int BC, bool FORCE, int MODE, int NCW>
 __global__ void __launch_bounds__(32 * (NCW + 1), stage_min_blocks(NCW, FORCE, MODE)) k_step_stage(const StepArgs<f2> a, const FastDiv div_tpp,
                                                                const unsigned ntiles, const int R, const int nsi)
