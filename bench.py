@@ -136,7 +136,7 @@ def ncu_entry(precision):
 def ncu_traffic(precision, n):
     """dram bytes per launch of the step kernel (n^3 TGV) from the committed ncu record, or None."""
     ent = ncu_entry(precision)
-    return float(ent["bytes_per_cell"]) * n ** 3 if ent else None
+    return float(ent["bytes_per_cell"]) * n ** 3 if ent and "bytes_per_cell" in ent else None
 
 
 # FP32 lane operations per second of the FMA pipes: 152 SMs x 128 lanes x 2.07 GHz (maximum SM clock)

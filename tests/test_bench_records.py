@@ -20,6 +20,9 @@ def test_record_is_consistent_and_reported_only_for_its_source():
         assert bench.ncu_traffic("fp32", 256) is None
         return
     for prec, ent in rec["entries"].items():
+        if "bytes_per_cell" not in ent:  # an instruction-count entry only
+            assert bench.ncu_traffic(prec, 256) is None
+            continue
         b = bench.BYTES[prec]
         # the DRAM traffic of a launch is the algorithmic 27 loads and (up to what stays in L2) 27
         # stores per cell
