@@ -284,6 +284,21 @@ FPCLBM_API int fpclbm_test_alloc_hook(int fail_after, long long* live);
  * caller-owned int[4]. */
 FPCLBM_API int fpclbm_get_launch(fpclbm_t h, int out[4]);
 
+/* The learned closure's weights in the device layout the fused inference reads
+ * (no counterpart in the paper; the layout test of the host packing runs it
+ * without a GPU).  w: the 4865 bf16 bit patterns of fpclbm_set_closure, in
+ * its order; out: caller-owned, out_words = 3012 32-bit words: [0, 512) the
+ * layer-1 B fragments of mma.sync.m16n8k16 per (n-tile nt, lane): words
+ * (nt * 32 + lane) * 2 + {0, 1}, each two bf16 of consecutive k (lower k in the
+ * low half), k = 2t, 2t+1 and 2t+8, 2t+9 for lane = 4g + t, output n = 8 nt + g,
+ * with b1 at k = 9; [512, 2560) the layer-2 B fragments, words
+ * ((nt * 4 + kt) * 32 + lane) * 2 + {0, 1}, k = 16 kt + the same offsets;
+ * [2560, 2624) b1, [2624, 2688) b2, [2688, 2752) W3 and [2752] b3 as fp32 bit
+ * patterns; [2756, 3012) per (nt, lane) the bf16 of b2[8 nt + g] for t = 0,
+ * else 0 (the first word of a B fragment whose only non-zero K row is 64).
+ * Pure host code.  Errors: ARG for a NULL pointer or other sizes. */
+FPCLBM_API int fpclbm_closure_pack(const unsigned short* w, int n_params, unsigned int* out, int out_words);
+
 /* Install the learned closure used by FPCLBM_DIFF_FP_LEARNED: a per-cell
  * MLP 9 -> 64 -> 64 -> 1 (tanh hidden layers) whose inputs are the six
  * non-equilibrium second-order central moments and u, and whose output

@@ -1055,22 +1055,14 @@ int fpclbm_set_populations(fpclbm_t h, const double* f)
     return FPCLBM_OK;
 }
 
-int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
+// The learned closure's weights (4865 bf16 bit patterns) in the device layout of closure.cuh
+// (CP_WORDS 32-bit words, zero-initialised by the caller): per-lane mma fragments of both layers,
+// the fp32 biases and output layer, and layer 2's bias fragments.
+static void pack_closure(const unsigned short* w, uint32_t* pk)
 {
-    if (!h) return FPCLBM_ERR_ARG;
-    h->err.clear();
-    if (!w) return fail(h, FPCLBM_ERR_ARG, "weights are NULL");
-    if (n_params != 4865) return fail(h, FPCLBM_ERR_ARG, "closure needs exactly 4865 parameters");
-    for (int i = 0; i < n_params; ++i) {
-        const unsigned bits = (unsigned)w[i] << 16;  // bf16 -> fp32 is exact
-        float v;
-        std::memcpy(&v, &bits, sizeof v);
-        if (!std::isfinite(v)) return fail(h, FPCLBM_ERR_ARG, "non-finite closure weight");
-    }
     // re-pack into the per-lane mma fragment order of closure.cuh: for lane (g = lane/4,
     // t = lane%4) and n-tile nt, output n = 8 nt + g; a 32-bit word holds two bf16 of
     // consecutive k (lower k in the low half): k = 2t, 2t+1 and k = 2t+8, 2t+9
-    std::vector<uint32_t> pk(CP_WORDS, 0u);
     auto wb = [&](int idx) -> uint32_t { return w[idx]; };
     // layer 1: K column 9 carries b1 (the kernel's input 9 is the constant 1)
     auto w1 = [&](int n, int k) -> uint32_t { return k < 9 ? wb(CL_W1 + 9 * n + k) : k == 9 ? wb(CL_B1 + n) : 0u; };
@@ -1096,6 +1088,31 @@ int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
         pk[CP_W3 + j] = wb(CL_W3 + j) << 16;
     }
     pk[CP_B3] = wb(CL_B3) << 16;
+}
+
+int fpclbm_closure_pack(const unsigned short* w, int n_params, unsigned int* out, int out_words)
+{
+    if (!w || !out || n_params != CL_N || out_words != CP_WORDS) return FPCLBM_ERR_ARG;
+    std::vector<uint32_t> pk(CP_WORDS, 0u);
+    pack_closure(w, pk.data());
+    std::memcpy(out, pk.data(), sizeof(uint32_t) * CP_WORDS);
+    return FPCLBM_OK;
+}
+
+int fpclbm_set_closure(fpclbm_t h, const unsigned short* w, int n_params)
+{
+    if (!h) return FPCLBM_ERR_ARG;
+    h->err.clear();
+    if (!w) return fail(h, FPCLBM_ERR_ARG, "weights are NULL");
+    if (n_params != 4865) return fail(h, FPCLBM_ERR_ARG, "closure needs exactly 4865 parameters");
+    for (int i = 0; i < n_params; ++i) {
+        const unsigned bits = (unsigned)w[i] << 16;  // bf16 -> fp32 is exact
+        float v;
+        std::memcpy(&v, &bits, sizeof v);
+        if (!std::isfinite(v)) return fail(h, FPCLBM_ERR_ARG, "non-finite closure weight");
+    }
+    std::vector<uint32_t> pk(CP_WORDS, 0u);
+    pack_closure(w, pk.data());
     if (!h->d_closure) {
         cudaError_t e = rt_malloc(&h->d_closure, sizeof(uint32_t) * CP_WORDS);
         if (e != cudaSuccess) return fail(h, FPCLBM_ERR_ALLOC, "closure weights");

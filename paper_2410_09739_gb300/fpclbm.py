@@ -52,7 +52,7 @@ EXPORTED = ("fpclbm_create", "fpclbm_create_ensemble", "fpclbm_init_fields", "fp
             "fpclbm_get_populations", "fpclbm_get_populations_at", "fpclbm_set_populations", "fpclbm_get_step_count", "fpclbm_get_launch", "fpclbm_set_closure",
             "fpclbm_state_bytes", "fpclbm_get_state", "fpclbm_set_state", "fpclbm_test_alloc_hook",
             "fpclbm_destroy", "fpclbm_last_error", "fpclbm_diagnostics_noalloc", "fpclbm_closure_sample",
-            "fpclbm_closure_train", "fpclbm_closure_grad",
+            "fpclbm_closure_train", "fpclbm_closure_grad", "fpclbm_closure_pack",
             "fpclbm2d_create", "fpclbm2d_init_fields", "fpclbm2d_set_params", "fpclbm2d_set_rates",
             "fpclbm2d_set_force", "fpclbm2d_set_boundary", "fpclbm2d_step", "fpclbm2d_moments", "fpclbm2d_get_populations",
             "fpclbm2d_set_populations", "fpclbm2d_destroy", "fpclbm2d_last_error")
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
     L.fpclbm_closure_train.argtypes = [_P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ushort), _D, _P]
     L.fpclbm_closure_grad.argtypes = [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_ushort), _P, _D, _P]
+    L.fpclbm_closure_pack.argtypes = [ctypes.POINTER(ctypes.c_ushort), ctypes.c_int, ctypes.POINTER(ctypes.c_uint),
+                                      ctypes.c_int]
     L.fpclbm_destroy.argtypes = [_P]
     L.fpclbm_last_error.argtypes = [_P]
     L.fpclbm_last_error.restype = ctypes.c_char_p
@@ -284,6 +286,21 @@ def fpclbm_get_launch(h) -> dict:
 def fpclbm_set_closure(h, bf16_bits):
     w = np.ascontiguousarray(np.asarray(bf16_bits, dtype=np.uint16))
     return _check(h, load().fpclbm_set_closure(h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_ushort)), w.size))
+
+
+CLOSURE_PACK_WORDS = 3012
+
+
+def fpclbm_closure_pack(bf16_bits) -> np.ndarray:
+    """The closure's 4865 bf16 weights in the device layout of the fused inference (uint32 words;
+    host code, no GPU needed)."""
+    w = np.ascontiguousarray(np.asarray(bf16_bits, dtype=np.uint16))
+    out = np.zeros(CLOSURE_PACK_WORDS, dtype=np.uint32)
+    rc = load().fpclbm_closure_pack(w.ctypes.data_as(ctypes.POINTER(ctypes.c_ushort)), w.size,
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)), out.size)
+    if rc != FPCLBM_OK:
+        raise FpclbmError(rc, "fpclbm_closure_pack: %d weights" % w.size)
+    return out
 
 
 def noalloc_args_check(f_numel: int, f_device: int, out_numel: int, out_device: int, current_device: int,
